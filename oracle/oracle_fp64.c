@@ -1,0 +1,298 @@
+/*
+ * FP64 oracle of the visibility-bitmask gather.
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by the tests, the smoke check and the
+ * benchmark's CPU-baseline leg; never by the product path.
+ *
+ * It follows Algorithm 1 (Section 3.1) in the paper's order, with the
+ * directionally occluded ambient term of Section 3.2 and the sample ordering
+ * of Section 3.3.  Geometry and angles are in double precision; the inputs are
+ * the binary32 G-buffer values promoted exactly.  The sector hit rule is
+ * evaluated per sector by brute force (overlap of [A, B] with [k, k+1]), and
+ * indirect light is credited per sector to the first sample that sets it,
+ * which equals Algorithm 1's countbits(b_j & ~b_i) form without bit tricks.
+ *
+ * Readings of the paper where it is silent or garbled (each is listed in the
+ * design notes):
+ *   - N_d slices i = 0..N_d-1 at azimuth (i + xi_phi) pi / N_d; N_s steps per
+ *     side, j = 0..N_s-1, at offset (j + 1 + xi_s) r / (N_s + 1) (Algorithm 1,
+ *     "stepsize r/(N_s+1)", "directions with random offset").
+ *   - Both sides of the slice, side -omega first, then +omega, near to far
+ *     (Section 3.1 "samples are still taken on each side"; Section 3.3 needs
+ *     near samples to occlude far ones).
+ *   - The back sample lies *behind* the front one, away from the camera along
+ *     the centre pixel's view ray: s_b = s_f + t p/|p| (Figure 4 caption and
+ *     the word "back"; the printed minus sign would put it in front).
+ *   - Elevation h = sigma acos(l.v/|l|) measured from the view vector v in the
+ *     slice; the sector frame is centred on the projected normal (Eq. 4),
+ *     X = (h - gamma) N_b / pi + N_b / 2, clamped to [0, N_b].
+ *   - Hit rule 0: a sector is set iff at least half of it is covered
+ *     (Section 3.1 "round criterion", Figure 4 caption).  Hit rule 1: the
+ *     floor/ceil form of Algorithm 1 without its stray +pi/2 in the width.
+ *   - Indirect light weight: (newly set sectors / N_b) c_j max(0, n_p.l)
+ *     max(0, -n_j.l), n_l read as the sample's normal n_j (Section 3.3).
+ *   - Sample pixel: nearest pixel (round half to even) of sigma o omega; the
+ *     sample is skipped when off-screen, equal to the centre pixel or sky.
+ *     Which pixel a step reads is an integer decision taken from floating
+ *     point, so it is taken here in binary32 exactly as the GPU takes it.
+ *   - Thickness t(z) = t + k_t z (Section 3.1, linear increase with
+ *     distance); t = +INF puts the back endpoint at the hemisphere edge of
+ *     the sample's side (GTAO without falloff, Section 3.1).
+ *   - Ambient (Section 3.2): N_a equal sector groups; the source is sampled in
+ *     the direction at the centre of each group and weighted by the group's
+ *     unoccluded sector count over N_b.
+ *   - AO output is Algorithm 1's sum of (1 - countbits(b_i)/N_b) / N_d, i.e.
+ *     the unoccluded fraction (1 = fully visible).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "oracle.h"
+
+typedef struct { double x, y, z; } d3;
+static d3 mk(double x, double y, double z) { d3 r = {x, y, z}; return r; }
+static d3 sub3(d3 a, d3 b) { return mk(a.x - b.x, a.y - b.y, a.z - b.z); }
+static d3 add3(d3 a, d3 b) { return mk(a.x + b.x, a.y + b.y, a.z + b.z); }
+static d3 mul3(d3 a, double s) { return mk(a.x * s, a.y * s, a.z * s); }
+static double dot3(d3 a, d3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+static double len3(d3 a) { return sqrt(dot3(a, a)); }
+static double clampd(double v, double lo, double hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+static int is_geometry(float z) { return z > 0.0f && z < INFINITY; }
+
+/* View-space position of the pixel centre (u, v) at linear depth z (camera looks along -z). */
+static d3 unproject(const orc_problem *pb, double u, double v, double z) {
+    return mk((u - pb->cx) / pb->fx * z, -(v - pb->cy) / pb->fy * z, -z);
+}
+
+/* Per-sector hit rule, brute force over the N_b sectors [k, k+1). */
+uint64_t orc64_sector_mask(double A, double B, int nb, int hit_rule) {
+    uint64_t m = 0;
+    if (hit_rule == 0) {
+        for (int k = 0; k < nb; ++k) {
+            double lo = A > k ? A : (double)k;
+            double hi = B < k + 1 ? B : (double)(k + 1);
+            if (hi - lo >= 0.5) m |= (uint64_t)1 << k;
+        }
+    } else {
+        /* Algorithm 1: a = floor(A), width = ceil(B - A), kept inside the N_b sectors */
+        double a = floor(A);
+        double w = ceil(B - A);
+        for (int k = 0; k < nb; ++k)
+            if (k >= a && k < a + w) m |= (uint64_t)1 << k;
+    }
+    return m;
+}
+
+static double frac_dist(double v) { return fabs(v - nearbyint(v)); }
+
+/* Distance of this sample's hit-rule decisions from their rounding boundaries. */
+static double decision_margin(double A, double B, int hit_rule) {
+    if (hit_rule == 0) {
+        double m = fabs((B - A) - 0.5);
+        double ma = frac_dist(A - 0.5), mb = frac_dist(B + 0.5);
+        if (ma < m) m = ma;
+        if (mb < m) m = mb;
+        return m;
+    }
+    double m = frac_dist(A);
+    double mw = frac_dist(B - A);
+    return mw < m ? mw : m;
+}
+
+/* Real spherical harmonics, 3 bands, in the order
+ * Y00, Y1-1 (y), Y10 (z), Y11 (x), Y2-2 (xy), Y2-1 (yz), Y20 (3z^2-1), Y21 (xz), Y22 (x^2-y^2). */
+static void sh9(d3 w, double Y[9]) {
+    const double c0 = 0.5 * sqrt(1.0 / M_PI);
+    const double c1 = sqrt(3.0 / (4.0 * M_PI));
+    const double c2 = 0.5 * sqrt(15.0 / M_PI);
+    const double c3 = 0.25 * sqrt(5.0 / M_PI);
+    const double c4 = 0.25 * sqrt(15.0 / M_PI);
+    Y[0] = c0;
+    Y[1] = c1 * w.y;
+    Y[2] = c1 * w.z;
+    Y[3] = c1 * w.x;
+    Y[4] = c2 * w.x * w.y;
+    Y[5] = c2 * w.y * w.z;
+    Y[6] = c3 * (3.0 * w.z * w.z - 1.0);
+    Y[7] = c2 * w.x * w.z;
+    Y[8] = c4 * (w.x * w.x - w.y * w.y);
+}
+
+static int validate(const orc_problem *pb) {
+    if (!pb || pb->width <= 0 || pb->height <= 0 || !pb->depth || !pb->normal || !pb->radiance) return 1;
+    if (pb->num_slices < 1 || pb->num_slices > 16) return 2;
+    if (pb->steps_per_side < 1 || pb->steps_per_side > 64) return 3;
+    if (pb->sector_count != 32 && pb->sector_count != 64) return 4;
+    if (pb->hit_rule != 0 && pb->hit_rule != 1) return 5;
+    if (!(pb->radius > 0.0f) || !(pb->radius < INFINITY)) return 6;
+    if (!(pb->thickness > 0.0f) || !(pb->thickness_slope >= 0.0f) || !(pb->thickness_slope < INFINITY)) return 7;
+    if (pb->ambient_cones < 0 || pb->ambient_cones > 8) return 8;
+    if (pb->ambient_cones > 0 && (pb->sector_count % pb->ambient_cones != 0 || !pb->sh)) return 8;
+    if (pb->step_mode != 0 && pb->step_mode != 1) return 9;
+    return 0;
+}
+
+int orc64_pixels(const orc_problem *pb, int n, const int32_t *xy, double *out0, double *out1,
+                 uint64_t *masks, double *margin) {
+    int bad = validate(pb);
+    if (bad) return bad;
+    const int W = pb->width, H = pb->height, nd = pb->num_slices, ns = pb->steps_per_side;
+    const int nb = pb->sector_count, na = pb->ambient_cones;
+    const int inf_t = isinf(pb->thickness);
+
+    for (int pi = 0; pi < n; ++pi) {
+        const int x = xy[2 * pi], y = xy[2 * pi + 1];
+        if (x < 0 || y < 0 || x >= W || y >= H) return 10;
+        double *o0 = out0 ? out0 + 4 * pi : NULL, *o1 = out1 ? out1 + 4 * pi : NULL;
+        const size_t pix = (size_t)y * W + x;
+        const float zf = pb->depth[pix];
+
+        /* Sky: nothing to occlude or bounce; fully visible. */
+        if (!is_geometry(zf)) {
+            if (o0) { o0[0] = o0[1] = o0[2] = 0.0; o0[3] = 1.0; }
+            if (o1) { o1[0] = o1[1] = o1[2] = o1[3] = 0.0; }
+            for (int i = 0; i < nd; ++i) {
+                if (masks) masks[(size_t)pi * nd + i] = 0;
+                if (margin) margin[(size_t)pi * nd + i] = INFINITY;
+            }
+            continue;
+        }
+
+        /* Algorithm 1: t, N_b, p, n_p, r. */
+        const double z = zf;
+        const d3 p = unproject(pb, x + 0.5, y + 0.5, z);
+        const double plen = len3(p);
+        const d3 vhat = mul3(p, -1.0 / plen);
+        const float *nrm = pb->normal + 4 * pix;
+        const d3 np_ = mk(nrm[0], nrm[1], nrm[2]);
+        const double tp = inf_t ? INFINITY : (double)pb->thickness + (double)pb->thickness_slope * z;
+        const int cls = (y & 3) * 4 + (x & 3);
+        const float xi_phi = pb->noise ? pb->noise[2 * cls] : 0.0f;
+        const float xi_s = pb->noise ? pb->noise[2 * cls + 1] : 0.0f;
+
+        /* Step sizes: the sample pixel is an integer decision, taken in binary32 as on the GPU. */
+        const float Rfx = pb->radius * pb->fx;
+        const float rpx = fminf(Rfx / zf, 1048576.0f);
+        const float dn = 1.0f / (float)(ns + 1);
+        const float xidn = xi_s * dn;
+
+        double AO = 0.0, GI[3] = {0, 0, 0}, AMB[3] = {0, 0, 0};
+        for (int i = 0; i < nd; ++i) {
+            /* Slice direction with random offset, rounded to binary32 (the direction table). */
+            const double phi = ((double)i + (double)xi_phi) * M_PI / (double)nd;
+            const float cphi = (float)cos(phi), sphi = (float)sin(phi);
+
+            /* Slice plane: v and the in-plane direction s toward screen direction +omega. */
+            const d3 w3 = mk((double)cphi / pb->fx, -(double)sphi / pb->fy, 0.0);
+            d3 s = sub3(w3, mul3(vhat, dot3(w3, vhat)));
+            s = mul3(s, 1.0 / len3(s));
+
+            /* Projected normal angle gamma = sign(n.s) acos(n.v / |projN|), 0 if projN = 0. */
+            const double nv = dot3(np_, vhat), nsd = dot3(np_, s);
+            const double pn = sqrt(nv * nv + nsd * nsd);
+            double gamma = 0.0;
+            if (pn > 0.0) {
+                gamma = acos(clampd(nv / pn, -1.0, 1.0));
+                if (nsd < 0.0) gamma = -gamma;
+            }
+
+            unsigned char occ[64];
+            memset(occ, 0, sizeof(occ));
+            double mrg = INFINITY;
+
+            for (int side = 0; side < 2; ++side) {
+                const int sigma = side == 0 ? -1 : 1;
+                const float wsx = sigma > 0 ? cphi : -cphi;
+                const float wsy = sigma > 0 ? sphi : -sphi;
+                for (int j = 0; j < ns; ++j) {
+                    /* Which pixel this step reads (binary32, nearest pixel, ties to even). */
+                    const float jp1 = (float)(j + 1);
+                    const float uj = fmaf(jp1, dn, xidn);
+                    const float off = pb->step_mode == 0 ? uj * rpx : (uj * uj) * rpx;
+                    const float dxf = rintf(off * wsx), dyf = rintf(off * wsy);
+                    if (dxf == 0.0f && dyf == 0.0f) continue;
+                    const int qx = x + (int)dxf, qy = y + (int)dyf;
+                    if (qx < 0 || qy < 0 || qx >= W || qy >= H) continue;
+                    const size_t q = (size_t)qy * W + qx;
+                    const float zq = pb->depth[q];
+                    if (!is_geometry(zq)) continue;
+
+                    /* Front sample s_f and its elevation in the slice. */
+                    const d3 sf = unproject(pb, qx + 0.5, qy + 0.5, (double)zq);
+                    const d3 l = sub3(sf, p);
+                    const double llen = len3(l);
+                    const double hf = sigma * acos(clampd(dot3(l, vhat) / llen, -1.0, 1.0));
+                    const double K = nb / M_PI;
+                    double Xf = clampd((hf - gamma) * K + 0.5 * nb, 0.0, (double)nb);
+                    double Xb;
+                    if (inf_t) {
+                        Xb = sigma > 0 ? (double)nb : 0.0;
+                    } else {
+                        /* Back sample s_b = s_f + t p/|p| (behind the front one). */
+                        const d3 sb = add3(sf, mul3(p, tp / plen));
+                        const d3 lb = sub3(sb, p);
+                        const double hb = sigma * acos(clampd(dot3(lb, vhat) / len3(lb), -1.0, 1.0));
+                        Xb = clampd((hb - gamma) * K + 0.5 * nb, 0.0, (double)nb);
+                    }
+                    const double A = Xf < Xb ? Xf : Xb, B = Xf < Xb ? Xb : Xf;
+                    const uint64_t bj = orc64_sector_mask(A, B, nb, pb->hit_rule);
+                    const double m = decision_margin(A, B, pb->hit_rule);
+                    if (m < mrg) mrg = m;
+
+                    /* Indirect light: each newly occluded sector carries c_j cos cos / N_b. */
+                    int newly = 0;
+                    for (int k = 0; k < nb; ++k)
+                        if (((bj >> k) & 1u) && !occ[k]) { occ[k] = 1; ++newly; }
+                    if (newly > 0 && pb->gi) {
+                        const float *cj = pb->radiance + 4 * q;
+                        const float *nj = pb->normal + 4 * q;
+                        const d3 lh = mul3(l, 1.0 / llen);
+                        const double cp = fmax(0.0, dot3(np_, lh));
+                        const double cq = fmax(0.0, -dot3(mk(nj[0], nj[1], nj[2]), lh));
+                        for (int k = 0; k < newly; ++k)
+                            for (int c = 0; c < 3; ++c) GI[c] += (double)cj[c] * cp * cq / nb;
+                    }
+                }
+            }
+
+            int set = 0;
+            for (int k = 0; k < nb; ++k) set += occ[k];
+            AO += 1.0 - (double)set / nb;
+
+            if (na > 0) {
+                /* Directionally occluded ambient: sample the source at each group's centre. */
+                const int g = nb / na;
+                for (int k = 0; k < na; ++k) {
+                    int unocc = 0;
+                    for (int s2 = k * g; s2 < (k + 1) * g; ++s2) unocc += !occ[s2];
+                    const double theta = gamma - 0.5 * M_PI + (k + 0.5) * M_PI / na;
+                    const d3 a = add3(mul3(vhat, cos(theta)), mul3(s, sin(theta)));
+                    const float *R = pb->view_to_world;
+                    const d3 wv = mk(R[0] * a.x + R[1] * a.y + R[2] * a.z, R[3] * a.x + R[4] * a.y + R[5] * a.z,
+                                     R[6] * a.x + R[7] * a.y + R[8] * a.z);
+                    double Y[9];
+                    sh9(wv, Y);
+                    for (int c = 0; c < 3; ++c) {
+                        double L = 0.0;
+                        for (int mm = 0; mm < 9; ++mm) L += (double)pb->sh[3 * mm + c] * Y[mm];
+                        AMB[c] += L * unocc / nb;
+                    }
+                }
+            }
+
+            if (masks) {
+                uint64_t bm = 0;
+                for (int k = 0; k < nb; ++k)
+                    if (occ[k]) bm |= (uint64_t)1 << k;
+                masks[(size_t)pi * nd + i] = bm;
+            }
+            if (margin) margin[(size_t)pi * nd + i] = mrg;
+        }
+        if (o0) { o0[0] = GI[0] / nd; o0[1] = GI[1] / nd; o0[2] = GI[2] / nd; o0[3] = AO / nd; }
+        if (o1) { o1[0] = AMB[0] / nd; o1[1] = AMB[1] / nd; o1[2] = AMB[2] / nd; o1[3] = 0.0; }
+    }
+    return 0;
+}

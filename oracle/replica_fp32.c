@@ -1,0 +1,360 @@
+/*
+ * Binary32 replica of the visibility-bitmask gather.
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by the tests, the smoke check and the
+ * benchmark's CPU-baseline leg; never by the product path.
+ *
+ * Algorithm 1 of the paper (Section 3.1) with the ambient cones of Section 3.2,
+ * in the binary32 operation sequence that decides the bitmasks: round to
+ * nearest even, explicit fused multiply-adds where written (fmaf), no other
+ * contraction (build with -ffp-contract=off), no flush to zero.  The sector
+ * masks are built in O(1) as one run of ones (Section 3.1, "all occluded
+ * sectors are set at once").  The GPU must reproduce these masks bit for bit;
+ * its continuous outputs are compared against the FP64 oracle.
+ *
+ * Every reading of the paper is the same as in oracle_fp64.c.  The choices
+ * specific to binary32 are:
+ *   - the arccosine is Abramowitz and Stegun 4.4.46, sqrt(1-x) times a degree-7
+ *     polynomial (|error| <= 2e-8 in exact arithmetic), with acos(-x) = pi - acos(x);
+ *   - normalisation uses an own reciprocal square root: the integer seed
+ *     0x5f3759df - (bits >> 1) (Lomont, "Fast inverse square root", 2003)
+ *     refined by three Newton steps y <- y (1.5 - 0.5 x y^2);
+ *   - the back endpoint uses l_b.v = l.v - t and |l_b|^2 = |l|^2 - 2t (l.v) + t^2,
+ *     which follow from l_b = l - t v (v = -p/|p|).
+ * Op counts (the algorithmic work used by the roofline) are accumulated per
+ * block, one per IEEE add/sub/mul/fma/div/sqrt, compare, select, min/max,
+ * conversion, shift, logic op and popcount.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "oracle.h"
+
+#define RSQRT_OPS 13
+#define ACOS_OPS 12
+
+/* Abramowitz and Stegun 4.4.46 coefficients a0..a7. */
+static const float AS0 = 1.5707963050f, AS1 = -0.2145988016f, AS2 = 0.0889789874f, AS3 = -0.0501743046f;
+static const float AS4 = 0.0308918810f, AS5 = -0.0170881256f, AS6 = 0.0066700901f, AS7 = -0.0012624911f;
+
+static float f_from_u(uint32_t u) { float f; memcpy(&f, &u, 4); return f; }
+static uint32_t u_from_f(float f) { uint32_t u; memcpy(&u, &f, 4); return u; }
+
+float orc32_rsqrt(float x) {
+    x = fmaxf(x, 1.17549435e-38f); /* smallest normal: keeps 0 finite */
+    float y = f_from_u(0x5f3759dfu - (u_from_f(x) >> 1));
+    const float hx = 0.5f * x;
+    for (int k = 0; k < 3; ++k) {
+        const float t = y * y;
+        const float u = fmaf(-hx, t, 1.5f);
+        y = y * u;
+    }
+    return y;
+}
+
+float orc32_acos(float c) {
+    const float a = fabsf(c);
+    const float s = sqrtf(1.0f - a);
+    float P = fmaf(AS7, a, AS6);
+    P = fmaf(P, a, AS5);
+    P = fmaf(P, a, AS4);
+    P = fmaf(P, a, AS3);
+    P = fmaf(P, a, AS2);
+    P = fmaf(P, a, AS1);
+    P = fmaf(P, a, AS0);
+    const float r = s * P;
+    return c < 0.0f ? 3.14159265358979323846f - r : r;
+}
+
+static float clamp1(float c) { return fmaxf(fminf(c, 1.0f), -1.0f); }
+
+static uint64_t low_bits(int k) { return k >= 64 ? ~(uint64_t)0 : (((uint64_t)1 << k) - 1); }
+
+uint64_t orc32_sector_mask(float A, float B, int nb, int hit_rule) {
+    int lo, hi;
+    if (hit_rule == 0) {
+        /* sectors whose centre k + 1/2 lies in [A, B], provided B - A >= 1/2:
+         * exactly the sectors covered at least half (Section 3.1 round criterion) */
+        if (!(B - A >= 0.5f)) return 0;
+        lo = (int)ceilf(A - 0.5f);
+        hi = (int)floorf(B + 0.5f);
+    } else {
+        lo = (int)floorf(A);
+        hi = lo + (int)ceilf(B - A);
+        if (hi > nb) hi = nb;
+    }
+    if (hi <= lo) return 0;
+    return low_bits(hi) & ~low_bits(lo);
+}
+
+static int is_geometry(float z) { return z > 0.0f && z < INFINITY; }
+
+static int validate(const orc_problem *pb) {
+    if (!pb || pb->width <= 0 || pb->height <= 0 || !pb->depth || !pb->normal || !pb->radiance) return 1;
+    if (pb->num_slices < 1 || pb->num_slices > 16) return 2;
+    if (pb->steps_per_side < 1 || pb->steps_per_side > 64) return 3;
+    if (pb->sector_count != 32 && pb->sector_count != 64) return 4;
+    if (pb->hit_rule != 0 && pb->hit_rule != 1) return 5;
+    if (!(pb->radius > 0.0f) || !(pb->radius < INFINITY)) return 6;
+    if (!(pb->thickness > 0.0f) || !(pb->thickness_slope >= 0.0f) || !(pb->thickness_slope < INFINITY)) return 7;
+    if (pb->ambient_cones < 0 || pb->ambient_cones > 8) return 8;
+    if (pb->ambient_cones > 0 && (pb->sector_count % pb->ambient_cones != 0 || !pb->sh)) return 8;
+    if (pb->step_mode != 0 && pb->step_mode != 1) return 9;
+    return 0;
+}
+
+int orc32_pixels(const orc_problem *pb, int n, const int32_t *xy, float *out0, float *out1,
+                 uint64_t *masks, int64_t *counts) {
+    int bad = validate(pb);
+    if (bad) return bad;
+    const int W = pb->width, H = pb->height, nd = pb->num_slices, ns = pb->steps_per_side;
+    const int nb = pb->sector_count, na = pb->ambient_cones;
+    const int inf_t = isinf(pb->thickness);
+    int64_t c_pix = 0, c_sky = 0, c_slice = 0, c_visit = 0, c_skip = 0, c_gi = 0, ops = 0;
+
+    /* Per-launch constants, binary32 unless noted. */
+    const float inv_fx = 1.0f / pb->fx, inv_fy = 1.0f / pb->fy;
+    const float kx0 = -(pb->cx * inv_fx), ninv_fy = -inv_fy, ky0 = pb->cy * inv_fy;
+    const float Rfx = pb->radius * pb->fx;
+    const float dn = 1.0f / (float)(ns + 1);
+    const float K = (float)((double)nb / M_PI); /* sectors per radian, FP64 rounded once */
+    const float half_nb = 0.5f * (float)nb, f_nb = (float)nb;
+    const float inv_nb = 1.0f / (float)nb, inv_nd = 1.0f / (float)nd;
+    const float t0 = pb->thickness, kt = pb->thickness_slope;
+
+    /* Direction table: cos, sin of (i + xi_phi) pi / N_d per noise class, FP64 rounded once. */
+    float dcos[16][16], dsin[16][16];
+    for (int c = 0; c < 16; ++c) {
+        const float xi = pb->noise ? pb->noise[2 * c] : 0.0f;
+        for (int i = 0; i < nd; ++i) {
+            const double phi = ((double)i + (double)xi) * M_PI / (double)nd;
+            dcos[c][i] = (float)cos(phi);
+            dsin[c][i] = (float)sin(phi);
+        }
+    }
+    /* Cone table: group-centre angles -pi/2 + (k + 1/2) pi / N_a relative to the normal. */
+    float ccos[8], csin[8];
+    for (int k = 0; k < na; ++k) {
+        const double th = -0.5 * M_PI + (k + 0.5) * M_PI / na;
+        ccos[k] = (float)cos(th);
+        csin[k] = (float)sin(th);
+    }
+    const float Y0 = (float)(0.5 * sqrt(1.0 / M_PI)), Y1 = (float)sqrt(3.0 / (4.0 * M_PI));
+    const float Y2 = (float)(0.5 * sqrt(15.0 / M_PI)), Y3 = (float)(0.25 * sqrt(5.0 / M_PI));
+    const float Y4 = (float)(0.25 * sqrt(15.0 / M_PI));
+
+    for (int pi = 0; pi < n; ++pi) {
+        const int x = xy[2 * pi], y = xy[2 * pi + 1];
+        if (x < 0 || y < 0 || x >= W || y >= H) return 10;
+        float *o0 = out0 ? out0 + 4 * pi : NULL, *o1 = out1 ? out1 + 4 * pi : NULL;
+        const size_t pix = (size_t)y * W + x;
+        const float z = pb->depth[pix];
+        ++c_pix;
+        ops += 3;
+        if (!is_geometry(z)) {
+            ++c_sky;
+            ops += 8;
+            if (o0) { o0[0] = o0[1] = o0[2] = 0.0f; o0[3] = 1.0f; }
+            if (o1) { o1[0] = o1[1] = o1[2] = o1[3] = 0.0f; }
+            if (masks) for (int i = 0; i < nd; ++i) masks[(size_t)pi * nd + i] = 0;
+            continue;
+        }
+
+        /* Pixel setup: p, v, n_p, projected radius, step unit, thickness. */
+        const float u = (float)x + 0.5f, v = (float)y + 0.5f;
+        const float ax = fmaf(u, inv_fx, kx0), by = fmaf(v, ninv_fy, ky0);
+        const float px = ax * z, py = by * z, pz = -z;
+        const float rd = orc32_rsqrt(fmaf(ax, ax, fmaf(by, by, 1.0f)));
+        const float vx = -(ax * rd), vy = -(by * rd), vz = rd;
+        const float *nrm = pb->normal + 4 * pix;
+        const float nx = nrm[0], ny = nrm[1], nz = nrm[2];
+        const float rpx = fminf(Rfx / z, 1048576.0f);
+        const int cls = (y & 3) * 4 + (x & 3);
+        const float xi_s = pb->noise ? pb->noise[2 * cls + 1] : 0.0f;
+        const float xidn = xi_s * dn;
+        float tp = 0.0f, t2 = 0.0f, m2t = 0.0f;
+        if (!inf_t) {
+            tp = fmaf(kt, z, t0);
+            t2 = tp * tp;
+            m2t = -2.0f * tp;
+        }
+        ops += 4 + 2 + 2 + RSQRT_OPS + 2 + 2 + 1 + 3 + 4;
+        (void)pz;
+
+        float AO = 0.0f, GIr = 0.0f, GIg = 0.0f, GIb = 0.0f, AMr = 0.0f, AMg = 0.0f, AMb = 0.0f;
+        for (int i = 0; i < nd; ++i) {
+            ++c_slice;
+            const float cphi = dcos[cls][i], sphi = dsin[cls][i];
+            /* Slice plane: s = normalize(w3 - (w3.v) v), w3 = view-space image of omega. */
+            const float w3x = cphi * inv_fx, w3y = -(sphi * inv_fy);
+            const float wv = fmaf(w3x, vx, w3y * vy);
+            const float sx0 = fmaf(-wv, vx, w3x), sy0 = fmaf(-wv, vy, w3y), sz0 = -(wv * vz);
+            const float rs = orc32_rsqrt(fmaf(sx0, sx0, fmaf(sy0, sy0, sz0 * sz0)));
+            const float sx = sx0 * rs, sy = sy0 * rs, sz = sz0 * rs;
+            /* Projected normal: gamma = sign(n.s) acos(n.v / |projN|). */
+            const float nv = fmaf(nx, vx, fmaf(ny, vy, nz * vz));
+            const float nsd = fmaf(nx, sx, fmaf(ny, sy, nz * sz));
+            const float pn2 = fmaf(nv, nv, nsd * nsd);
+            float cg = 1.0f, sg = 0.0f, gam = 0.0f;
+            if (pn2 > 0.0f) {
+                const float rpn = orc32_rsqrt(pn2);
+                cg = nv * rpn;
+                sg = nsd * rpn;
+                gam = orc32_acos(clamp1(cg));
+                if (nsd < 0.0f) gam = -gam;
+                ops += RSQRT_OPS + 2 + 2 + ACOS_OPS + 2;
+            }
+            const float off = fmaf(-gam, K, half_nb);
+            ops += 2 + 2 + 3 + 3 + RSQRT_OPS + 3 + 6 + 2 + 1 + 1 + 2;
+
+            uint64_t b = 0;
+            for (int side = 0; side < 2; ++side) {
+                const int pos = side == 1; /* side -omega first, then +omega */
+                const float wsx = pos ? cphi : -cphi, wsy = pos ? sphi : -sphi;
+                const float sK = pos ? K : -K;
+                const float edge = pos ? f_nb : 0.0f;
+                for (int j = 0; j < ns; ++j) {
+                    ++c_visit;
+                    /* Step offset along the direction and the nearest pixel (ties to even). */
+                    const float uj = fmaf((float)(j + 1), dn, xidn);
+                    const float o = pb->step_mode == 0 ? uj * rpx : (uj * uj) * rpx;
+                    const float dxf = rintf(o * wsx), dyf = rintf(o * wsy);
+                    ops += 2 + (pb->step_mode != 0) + 4 + 3;
+                    if (dxf == 0.0f && dyf == 0.0f) { ++c_skip; continue; }
+                    const int qx = x + (int)dxf, qy = y + (int)dyf;
+                    ops += 4 + 3;
+                    if (qx < 0 || qy < 0 || qx >= W || qy >= H) { ++c_skip; continue; }
+                    const size_t q = (size_t)qy * W + qx;
+                    const float zq = pb->depth[q];
+                    ops += 2 + 3;
+                    if (!is_geometry(zq)) { ++c_skip; continue; }
+
+                    /* Front sample: l = s_f - p, its cosine to v, its sector coordinate. */
+                    const float uq = u + dxf, vq = v + dyf;
+                    const float aq = fmaf(uq, inv_fx, kx0), bq = fmaf(vq, ninv_fy, ky0);
+                    const float lx = fmaf(aq, zq, -px), ly = fmaf(bq, zq, -py), lz = z - zq;
+                    const float dv = fmaf(lx, vx, fmaf(ly, vy, lz * vz));
+                    const float ll = fmaf(lx, lx, fmaf(ly, ly, lz * lz));
+                    const float rl = orc32_rsqrt(ll);
+                    const float cf = clamp1(dv * rl);
+                    const float Xf = fminf(fmaxf(fmaf(orc32_acos(cf), sK, off), 0.0f), f_nb);
+                    ops += 2 + 2 + 3 + 6 + RSQRT_OPS + 3 + ACOS_OPS + 3;
+
+                    /* Back sample (constant thickness behind the front one). */
+                    float Xb;
+                    if (inf_t) {
+                        Xb = edge;
+                    } else {
+                        const float dvb = dv - tp;
+                        const float llb = fmaf(m2t, dv, ll + t2);
+                        const float cb = clamp1(dvb * orc32_rsqrt(llb));
+                        Xb = fminf(fmaxf(fmaf(orc32_acos(cb), sK, off), 0.0f), f_nb);
+                        ops += 3 + RSQRT_OPS + 3 + ACOS_OPS + 3;
+                    }
+                    const float A = fminf(Xf, Xb), B = fmaxf(Xf, Xb);
+                    const uint64_t bj = orc32_sector_mask(A, B, nb, pb->hit_rule);
+                    const int newly = __builtin_popcountll(bj & ~b);
+                    b |= bj;
+                    ops += 2 + 12 + 3 + 1;
+
+                    /* Indirect light from the newly occluded sectors (Section 3.3). */
+                    if (newly > 0 && pb->gi) {
+                        ++c_gi;
+                        const float *cj = pb->radiance + 4 * q, *nj = pb->normal + 4 * q;
+                        const float cp = fmaxf(fmaf(nx, lx, fmaf(ny, ly, nz * lz)) * rl, 0.0f);
+                        const float cq = fmaxf(-(fmaf(nj[0], lx, fmaf(nj[1], ly, nj[2] * lz)) * rl), 0.0f);
+                        const float wgt = (((float)newly * inv_nb) * cp) * cq;
+                        GIr = fmaf(wgt, cj[0], GIr);
+                        GIg = fmaf(wgt, cj[1], GIg);
+                        GIb = fmaf(wgt, cj[2], GIb);
+                        ops += 5 + 5 + 4 + 3;
+                    }
+                }
+            }
+
+            /* Slice end: unoccluded fraction, then the ambient cones (Section 3.2). */
+            const int occ = __builtin_popcountll(b);
+            AO += (float)(nb - occ) * inv_nb;
+            ops += 5;
+            for (int k = 0; k < na; ++k) {
+                const int g = nb / na;
+                const uint64_t Mk = low_bits((k + 1) * g) & ~low_bits(k * g);
+                const int freek = __builtin_popcountll(~b & Mk);
+                const float ck = fmaf(cg, ccos[k], -(sg * csin[k]));
+                const float sk = fmaf(sg, ccos[k], cg * csin[k]);
+                const float ax3 = fmaf(ck, vx, sk * sx), ay3 = fmaf(ck, vy, sk * sy), az3 = fmaf(ck, vz, sk * sz);
+                const float *R = pb->view_to_world;
+                const float wx = fmaf(R[0], ax3, fmaf(R[1], ay3, R[2] * az3));
+                const float wy = fmaf(R[3], ax3, fmaf(R[4], ay3, R[5] * az3));
+                const float wz = fmaf(R[6], ax3, fmaf(R[7], ay3, R[8] * az3));
+                float Y[9];
+                Y[0] = Y0;
+                Y[1] = Y1 * wy;
+                Y[2] = Y1 * wz;
+                Y[3] = Y1 * wx;
+                Y[4] = Y2 * (wx * wy);
+                Y[5] = Y2 * (wy * wz);
+                Y[6] = Y3 * fmaf(3.0f * wz, wz, -1.0f);
+                Y[7] = Y2 * (wx * wz);
+                Y[8] = Y4 * fmaf(wx, wx, -(wy * wy));
+                const float wt = (float)freek * inv_nb;
+                float L[3];
+                for (int c = 0; c < 3; ++c) {
+                    float acc = pb->sh[c] * Y[0];
+                    for (int m = 1; m < 9; ++m) acc = fmaf(pb->sh[3 * m + c], Y[m], acc);
+                    L[c] = acc;
+                }
+                AMr = fmaf(wt, L[0], AMr);
+                AMg = fmaf(wt, L[1], AMg);
+                AMb = fmaf(wt, L[2], AMb);
+                ops += 3 + 4 + 6 + 9 + 17 + 2 + 27 + 3;
+            }
+            if (masks) masks[(size_t)pi * nd + i] = b;
+        }
+        if (o0) { o0[0] = GIr * inv_nd; o0[1] = GIg * inv_nd; o0[2] = GIb * inv_nd; o0[3] = AO * inv_nd; }
+        if (o1) { o1[0] = AMr * inv_nd; o1[1] = AMg * inv_nd; o1[2] = AMb * inv_nd; o1[3] = 0.0f; }
+        ops += 8;
+    }
+    if (counts) {
+        counts[0] = c_pix; counts[1] = c_sky; counts[2] = c_slice; counts[3] = c_visit;
+        counts[4] = c_skip; counts[5] = c_gi; counts[6] = ops;
+    }
+    return 0;
+}
+
+/* Test helper: sweep every binary32 value in [0, 1] (bit patterns 0 .. 0x3f800000).
+ * Counts places where orc32_acos increases with its argument and returns the largest
+ * absolute error against the C library's double-precision acos on every stride-th value. */
+void orc32_acos_sweep(int stride, double *max_err, int64_t *increases) {
+    float prev = orc32_acos(0.0f);
+    double me = 0.0;
+    int64_t inc = 0;
+    for (uint32_t u = 1; u <= 0x3f800000u; ++u) {
+        const float x = f_from_u(u);
+        const float a = orc32_acos(x);
+        if (a > prev) ++inc;
+        prev = a;
+        if (stride > 0 && (u % (uint32_t)stride) == 0) {
+            const double e = fabs((double)a - acos((double)x));
+            if (e > me) me = e;
+        }
+    }
+    *max_err = me;
+    *increases = inc;
+}
+
+/* Test helper: largest relative error of orc32_rsqrt over n values spread over [lo, hi]
+ * geometrically, against the double-precision 1/sqrt. */
+double orc32_rsqrt_sweep(double lo, double hi, int n) {
+    double me = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double t = (n > 1) ? (double)i / (n - 1) : 0.0;
+        const float x = (float)(lo * pow(hi / lo, t));
+        const double ref = 1.0 / sqrt((double)x);
+        const double e = fabs((double)orc32_rsqrt(x) - ref) / ref;
+        if (e > me) me = e;
+    }
+    return me;
+}

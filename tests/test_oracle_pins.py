@@ -1,0 +1,321 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+None of these compares the oracle with itself: each expected value comes from
+a closed form, a hand-worked fixture, a brute-force restatement on a tiny
+input, or an invariant the method must satisfy (Section 3.1-3.3).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import scenegen
+from scenegen import Params
+from tests import _geom as G
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+INF = float("inf")
+
+
+def _read_cases():
+    rows = []
+    with open(os.path.join(GOLDEN, "sector_rule_cases.txt")) as f:
+        for line in f:
+            line = line.split("#")[0].strip()
+            if line:
+                nb, rule, A, B, m = line.split()
+                rows.append((int(nb), int(rule), float(A), float(B), int(m, 16)))
+    return rows
+
+
+# --- hit rule (Section 3.1 round criterion, Figure 4, Algorithm 1) -------------------------
+
+@pytest.mark.parametrize("nb,rule,A,B,expect", _read_cases())
+def test_hit_rule_hand_cases(nb, rule, A, B, expect):
+    assert oracle.sector_mask64(A, B, nb, rule) == expect
+    assert oracle.sector_mask32(A, B, nb, rule) == expect
+
+
+@pytest.mark.parametrize("nb", [32, 64])
+@pytest.mark.parametrize("rule", [0, 1])
+def test_hit_rule_o1_equals_per_sector(nb, rule):
+    """The O(1) run of ones equals the per-sector brute force on a grid of exact endpoints,
+    including every tie (endpoints on sector centres and widths of exactly 1/2)."""
+    step = 1.0 / 8.0 if nb == 32 else 1.0 / 4.0
+    vals = np.arange(0.0, nb + step / 2, step)
+    fine = np.arange(0.0, 2.5, 1.0 / 128.0)
+    for grid in (vals, fine):
+        for A in grid:
+            for B in grid[grid >= A]:
+                a, b = float(A), float(B)
+                assert oracle.sector_mask32(a, b, nb, rule) == oracle.sector_mask64(a, b, nb, rule), (a, b)
+
+
+def test_hit_rule_random_endpoints():
+    rng = np.random.default_rng(5)
+    for _ in range(20000):
+        A, B = np.sort(rng.uniform(0, 32, 2).astype(np.float32))
+        m32 = oracle.sector_mask32(float(A), float(B), 32, 0)
+        assert m32 == G.half_covered_mask(float(A), float(B), 32)
+
+
+# --- own arithmetic of the binary32 replica ---------------------------------------------------
+
+def test_acos_error_bound_exhaustive():
+    """Every binary32 in [0, 1]: within 3e-7 rad of the libm double acos (A&S 4.4.46 bounds
+    the exact-arithmetic error by 2e-8; the rest is binary32 rounding).  The sweep also
+    counts increases: the binary32 evaluation is not strictly monotone (one-ulp upticks)."""
+    err, inc = oracle.acos32_sweep(64)
+    assert err < 3e-7
+    assert inc < 5000
+    for x in (-1.0, -0.5, 0.0, 0.5, 1.0):
+        assert abs(oracle.acos32(x) - math.acos(x)) < 3e-7
+    assert oracle.acos32(1.0) == 0.0
+
+
+def test_rsqrt_error_bound():
+    assert oracle.rsqrt32_sweep(1e-37, 1e37, 200000) < 3e-7
+    assert oracle.rsqrt32_sweep(0.5, 8.0, 200000) < 3e-7
+    assert math.isfinite(oracle.rsqrt32(0.0))
+
+
+# --- flat plane and empty sky (Section 3.1: samples in the tangent plane occlude nothing) ------
+
+@pytest.mark.parametrize("normal", [(0.0, 0.0, 1.0), (0.0, 0.6, 0.8), (0.5, -0.3, 0.81), (-0.9, 0.1, 0.42)])
+@pytest.mark.parametrize("thickness", [0.5, INF])
+def test_flat_plane_no_occlusion(normal, thickness):
+    """Slices at multiples of pi/4 sample pixels on the slice line, so every sample lies in the
+    plane of the centre pixel: no sector is half covered, AO = 1 and GI = 0 exactly."""
+    g = scenegen.hand_plane(41, 33, normal_view=normal, point_depth=6.0)
+    prm = Params(num_slices=4, steps_per_side=7, radius=2.0, thickness=thickness)
+    for fn in (oracle.fp64, oracle.fp32):
+        res = fn(oracle.Problem(g, prm, None))
+        o0, masks = res[0], res[2]
+        geo = np.isfinite(g.depth.ravel())
+        assert geo.sum() > 100
+        assert np.all(masks == 0)
+        assert np.all(o0[:, 3] == 1.0)
+        assert np.all(o0[:, :3] == 0.0)
+
+
+def test_quad_over_sky_full_visibility():
+    g = scenegen.hand_quad_over_sky(48, 40)
+    prm = Params(num_slices=4, steps_per_side=8, radius=1.5, thickness=0.3, ambient_cones=0)
+    for fn in (oracle.fp64, oracle.fp32):
+        o0, o1, masks = fn(oracle.Problem(g, prm, None))[:3]
+        assert np.all(masks == 0) and np.all(o0[:, 3] == 1.0) and np.all(o0[:, :3] == 0.0)
+
+
+def test_sky_pixels_fully_visible():
+    g = scenegen.hand_quad_over_sky(20, 20, x0=5, x1=10, y0=5, y1=10)
+    prm = Params(num_slices=3, steps_per_side=4)
+    o0, o1, masks, _ = oracle.fp64(oracle.Problem(g, prm, scenegen.ign_table()))
+    sky = ~np.isfinite(g.depth.ravel())
+    assert np.all(o0[sky] == [0, 0, 0, 1]) and np.all(o1[sky] == 0) and np.all(masks[sky] == 0)
+
+
+# --- infinite thickness is the horizon method quantised to sectors (Section 3.1) -------------
+
+def _horizon_masks(g, nd, ns, radius, nb):
+    """GTAO-style horizons (largest cosine per side over the same samples), quantised by the
+    half-covered rule; restated here in FP64 from the definition."""
+    H, W = g.depth.shape
+    cam = g.camera
+    out = np.zeros((H * W, nd), dtype=np.uint64)
+    for y in range(H):
+        for x in range(W):
+            z = float(g.depth[y, x])
+            if not (0 < z < INF):
+                continue
+            n = g.normal[y, x, :3].astype(np.float64)
+            offs = G.sample_offsets(radius, cam.fx, z, ns)
+            for i in range(nd):
+                cphi, sphi = G.slice_dir(i, nd)
+                p, v, s, gamma = G.frame(cam, x, y, z, n, cphi, sphi)
+                m = 0
+                for sigma in (-1, 1):
+                    best = -INF
+                    for qx, qy, zq in G.sample_pixels(x, y, W, H, g.depth, offs, cphi, sphi, sigma):
+                        l = G.unproject(cam, qx + 0.5, qy + 0.5, zq) - p
+                        best = max(best, float(np.dot(l, v) / np.linalg.norm(l)))
+                    if best == -INF:
+                        continue
+                    h = sigma * math.acos(max(-1.0, min(1.0, best)))
+                    X = G.sector_coord(h, gamma, nb)
+                    m |= G.half_covered_mask(X, nb, nb) if sigma > 0 else G.half_covered_mask(0.0, X, nb)
+                out[y * W + x, i] = m
+    return out
+
+
+@pytest.mark.parametrize("nb", [32, 64])
+def test_infinite_thickness_equals_quantised_horizon(nb):
+    g = scenegen.render(11, 28, 22, 6, 2)
+    prm = Params(num_slices=2, steps_per_side=6, radius=3.0, thickness=INF, sector_count=nb)
+    _, _, masks, margin = oracle.fp64(oracle.Problem(g, prm, None))
+    ref = _horizon_masks(g, 2, 6, 3.0, nb)
+    assert np.count_nonzero(ref) > 20
+    diff = masks != ref
+    assert np.all(margin[diff] < 1e-9)
+    assert diff.mean() < 1e-3
+
+
+# --- single infinite wall: closed-form occluded fraction (Section 3.1) ------------------------
+
+@pytest.mark.parametrize("thickness", [INF, 2.0])
+def test_step_wall_closed_form(thickness):
+    """Centre pixel on the back plane at the principal point (gamma = 0).  A wall face at
+    x = X_w rises H_w toward the camera; on slice phi the top edge is at in-plane distance
+    X_w/|cos phi|, so the occluded sectors on the wall side are N_b (pi/2 - h*)/pi with
+    h* = atan2(X_w/|cos phi|, H_w).  Holds for t = inf and any t >= H_w."""
+    W = H = 255
+    z0, xw, hw, nb = 4.0, 0.6, 1.5, 32
+    g = scenegen.hand_step_wall(W, H, z0, xw, hw)
+    prm = Params(num_slices=4, steps_per_side=48, radius=3.0, thickness=thickness, sector_count=nb)
+    c = (W - 1) // 2
+    _, _, masks, _ = oracle.fp64(oracle.Problem(g, prm, None), pixels=[(c, c)])
+    for i in range(4):
+        phi = i * math.pi / 4
+        cphi = abs(math.cos(phi))
+        expect = 0.0 if cphi < 1e-9 else nb * (math.pi / 2 - math.atan2(xw / cphi, hw)) / math.pi
+        got = bin(int(masks[0, i])).count("1")
+        assert abs(got - expect) <= 1.0, (i, got, expect)
+
+
+# --- single sample: closed-form indirect light (Algorithm 1 GI line, Section 3.3) -------------
+
+def test_single_sample_gi_closed_form():
+    """Sky everywhere except the centre pixel p and one pixel q on the first step of the
+    +omega side of slice 0.  The result is that sample alone: cnt sectors of its slab,
+    GI = cnt/N_b * c_q * max(0, n_p.l) * max(0, -n_q.l) / N_d."""
+    W = H = 31
+    fx = 15.5
+    cam = scenegen.Camera(fx, fx, 15.5, 15.5)
+    c = 15
+    radius, ns, nb, t = 2.0, 4, 32, 0.4
+    z, zq = 3.0, 2.2
+    offs = G.sample_offsets(radius, fx, z, ns)
+    dq = int(np.rint(offs[0]))
+    depth = np.full((H, W), np.inf, dtype=np.float32)
+    depth[c, c] = z
+    depth[c, c + dq] = zq
+    nrm = np.zeros((H, W, 4), dtype=np.float32)
+    nrm[c, c, :3] = (0.0, 0.0, 1.0)
+    nq = np.array([-0.6, 0.0, 0.8], dtype=np.float32)
+    nrm[c, c + dq, :3] = nq
+    rad = np.zeros((H, W, 4), dtype=np.float32)
+    cq = np.array([0.9, 0.4, 0.2], dtype=np.float32)
+    rad[c, c + dq, :3] = cq
+    g = scenegen.GBuffer(depth, nrm, rad, cam)
+    prm = Params(num_slices=1, steps_per_side=ns, radius=radius, thickness=t, sector_count=nb)
+
+    # closed form
+    n_p = np.array([0.0, 0.0, 1.0])
+    p, v, s, gamma = G.frame(cam, c, c, z, n_p, np.float32(1.0), np.float32(0.0))
+    sf = G.unproject(cam, c + dq + 0.5, c + 0.5, zq)
+    l = sf - p
+    hf = math.acos(np.dot(l, v) / np.linalg.norm(l))
+    sb = sf + t * p / np.linalg.norm(p)
+    lb = sb - p
+    hb = math.acos(np.dot(lb, v) / np.linalg.norm(lb))
+    A, B = sorted([G.sector_coord(hf, gamma, nb), G.sector_coord(hb, gamma, nb)])
+    m = G.half_covered_mask(A, B, nb)
+    cnt = bin(m).count("1")
+    assert cnt >= 2
+    lh = l / np.linalg.norm(l)
+    w = cnt / nb * max(0.0, float(np.dot(n_p, lh))) * max(0.0, float(-np.dot(nq.astype(np.float64), lh)))
+    gi = w * cq.astype(np.float64)
+    ao = 1.0 - cnt / nb
+
+    o0, _, masks, _ = oracle.fp64(oracle.Problem(g, prm, None), pixels=[(c, c)])
+    assert int(masks[0, 0]) == m
+    np.testing.assert_allclose(o0[0, :3], gi, rtol=1e-12, atol=1e-15)
+    assert abs(o0[0, 3] - ao) < 1e-15
+    r0, _, rmask = oracle.fp32(oracle.Problem(g, prm, None), pixels=[(c, c)])
+    assert int(rmask[0, 0]) == m
+    np.testing.assert_allclose(r0[0, :3], gi, atol=2e-6)
+
+
+# --- monotonicity (Section 3.1: samples only add occlusion; thicker slabs cover more) ---------
+
+def _subset(a, b):
+    return np.all((a & ~b) == 0)
+
+
+def test_masks_monotone_in_samples():
+    """N_s -> 2 N_s + 1 with zero noise reads a superset of the same step offsets."""
+    g = scenegen.render(21, 40, 32, 8, 3)
+    for fn in (oracle.fp64, oracle.fp32):
+        m_a = fn(oracle.Problem(g, Params(num_slices=3, steps_per_side=5, radius=2.5, thickness=0.4), None))[2]
+        m_b = fn(oracle.Problem(g, Params(num_slices=3, steps_per_side=11, radius=2.5, thickness=0.4), None))[2]
+        assert _subset(m_a, m_b)
+        assert np.count_nonzero(m_b) > np.count_nonzero(m_a) > 0
+
+
+def test_masks_monotone_in_thickness():
+    g = scenegen.render(22, 40, 32, 8, 3)
+    prev = None
+    for t in (0.05, 0.2, 0.6, 2.0, INF):
+        m = oracle.fp64(oracle.Problem(g, Params(num_slices=2, steps_per_side=8, thickness=t), scenegen.ign_table()))[2]
+        if prev is not None:
+            assert _subset(prev, m)
+        prev = m
+
+
+# --- ambient cones (Section 3.2) ------------------------------------------------------------
+
+def test_constant_environment_ambient_is_L_times_visibility():
+    """Band-0 SH only: every cone sees the same radiance L = c00 Y00, and the unoccluded
+    sector counts over all cones sum to N_b - popc(b), so ambient = L * AO."""
+    g = scenegen.render(31, 36, 30, 8, 2)
+    sh = np.zeros((9, 3), dtype=np.float32)
+    sh[0] = (0.8, 0.5, 0.3)
+    prm = Params(num_slices=3, steps_per_side=6, ambient_cones=4)
+    o0, o1, _, _ = oracle.fp64(oracle.Problem(g, prm, scenegen.ign_table(), sh))
+    L = sh[0].astype(np.float64) * 0.5 * math.sqrt(1.0 / math.pi)
+    geo = np.isfinite(g.depth.ravel())
+    np.testing.assert_allclose(o1[geo, :3], o0[geo, 3:4] * L[None, :], rtol=1e-12, atol=1e-14)
+    r0, r1, _ = oracle.fp32(oracle.Problem(g, prm, scenegen.ign_table(), sh))
+    np.testing.assert_allclose(r1[geo, :3], r0[geo, 3:4] * L[None, :], atol=2e-6)
+
+
+def test_linear_environment_ambient_closed_form():
+    """Unoccluded pixel on the optical axis facing the camera: gamma = 0 on every slice and the
+    N_a = 4 cone directions average to cos(pi/8)+cos(3pi/8) over 2 times v.  With a band-1 SH
+    the ambient is linear in direction: L = c00 Y00 + c1 sqrt(3/4pi) (R v)."""
+    W = H = 33
+    g = scenegen.hand_quad_over_sky(W, H, depth=3.0, x0=0, x1=W, y0=0, y1=H)
+    th = math.radians(20.0)
+    R = np.array([[1, 0, 0], [0, math.cos(th), -math.sin(th)], [0, math.sin(th), math.cos(th)]], dtype=np.float32)
+    g.camera.view_to_world = R
+    sh = np.zeros((9, 3), dtype=np.float32)
+    sh[0] = (0.7, 0.6, 0.5)
+    sh[1] = (0.10, -0.05, 0.0)   # y
+    sh[2] = (0.05, 0.10, -0.1)   # z
+    sh[3] = (-0.1, 0.0, 0.08)    # x
+    prm = Params(num_slices=4, steps_per_side=5, radius=1.0, ambient_cones=4)
+    c = W // 2
+    o0, o1, masks, _ = oracle.fp64(oracle.Problem(g, prm, None, sh), pixels=[(c, c)])
+    assert np.all(masks == 0)
+    k = (math.cos(math.pi / 8) + math.cos(3 * math.pi / 8)) / 2.0
+    wv = R.astype(np.float64) @ np.array([0.0, 0.0, 1.0]) * k
+    c0 = 0.5 * math.sqrt(1 / math.pi)
+    c1 = math.sqrt(3 / (4 * math.pi))
+    s64 = sh.astype(np.float64)
+    expect = s64[0] * c0 + c1 * (s64[1] * wv[1] + s64[2] * wv[2] + s64[3] * wv[0])
+    np.testing.assert_allclose(o1[0, :3], expect, rtol=1e-12, atol=1e-14)
+
+
+# --- the binary32 replica against the FP64 oracle on a seeded frame ---------------------------
+
+def test_replica_vs_fp64_on_256():
+    w = scenegen.workload_256()
+    prob = oracle.Problem(w.gbuf, w.params, w.noise)
+    o0, o1, m64, margin = oracle.fp64(prob)
+    r0, r1, m32 = oracle.fp32(prob)
+    same = np.all(m64 == m32, axis=1)
+    diff = m64 != m32
+    assert np.all(margin[diff] < 1e-3)
+    assert same.mean() > 0.99
+    assert np.abs(r0[same] - o0[same]).max() < 1e-5
