@@ -1,0 +1,307 @@
+"""Benchmark of the visibility-bitmask gather on GB300.
+
+Default workload: the 4K precision form (3840x2160, FP32 depth + FP16 normal and
+radiance, 4 slices, 32 steps per side, N_b = 32, 4 ambient cones against a seeded
+3-band SH environment, R = 2 m, t = 0.5 m) on a seeded procedural scene.
+One step = one gather over one frame.  Metric: Gsamples/s (2 N_d N_s samples per
+pixel, all pixels) and ms/frame.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--workload 4k|1080p|256] [--nb 32|64]
+
+Under torchrun (N > 1) every rank gathers its own frames (independent replicas,
+no collective on the data path); value = all ranks' samples / max-over-ranks time.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import scenegen  # noqa: E402
+
+SM_COUNT_GB300 = 152
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ssilvb", choices=["ssilvb", "reference"])
+    ap.add_argument("--workload", default="4k", choices=["4k", "1080p", "256"])
+    ap.add_argument("--nb", type=int, default=32)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def make_workload(name, nb):
+    if name == "4k":
+        return scenegen.workload_4k(sector_count=nb)
+    if name == "1080p":
+        return scenegen.workload_1080p()
+    return scenegen.workload_256()
+
+
+def samples_per_frame(w):
+    H, W = w.gbuf.depth.shape
+    return H * W * 2 * w.params.num_slices * w.params.steps_per_side
+
+
+class Clocks:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows if len(r) >= 9 for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm)}
+
+
+def algorithmic_ops_per_frame(w, n_pix=24576, seed=123):
+    """Algorithmic lane-ops of one frame: the binary32 replica's op count (one per IEEE
+    add/mul/fma/div/sqrt, compare, select, conversion, shift, logic op, popcount) on a
+    uniform random pixel sample, scaled to the frame."""
+    import oracle
+    H, W = w.gbuf.depth.shape
+    rng = np.random.default_rng(seed)
+    idx = rng.choice(H * W, size=min(n_pix, H * W), replace=False)
+    xy = np.stack([idx % W, idx // W], 1).astype(np.int32)
+    prob = oracle.Problem(w.gbuf, w.params, w.noise, w.sh)
+    _, _, _, c = oracle.fp32(prob, xy, counts=True)
+    scale = (H * W) / len(idx)
+    return c["ops"] * scale, {k: v * scale for k, v in c.items()}
+
+
+def cpu_baseline(w, target_s=15.0):
+    """The FP64 oracle, as it stands, single-threaded, on a bounded pixel sample of the workload."""
+    import oracle
+    H, W = w.gbuf.depth.shape
+    prob = oracle.Problem(w.gbuf, w.params, w.noise, w.sh)
+    rng = np.random.default_rng(7)
+    per_px = 2 * w.params.num_slices * w.params.steps_per_side
+    n = 256
+    while True:
+        idx = rng.choice(H * W, size=n, replace=False)
+        xy = np.stack([idx % W, idx // W], 1).astype(np.int32)
+        t0 = time.perf_counter()
+        oracle.fp64(prob, xy)
+        dt = time.perf_counter() - t0
+        if dt >= target_s or n >= H * W:
+            break
+        n = min(H * W, max(n * 2, int(n * target_s / max(dt, 1e-3) * 1.05)))
+    return {"value": n * per_px / dt / 1e9, "unit": "Gsamples/s", "cores": 1, "kind": "oracle",
+            "sample": f"FP64 oracle, 1 thread, {n} uniformly drawn pixels of the {W}x{H} frame "
+                      f"({n * per_px} samples, {dt:.1f} s)"}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, v):
+    if world <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_reference(args, world, rank):
+    """Reference arm: the CPU oracle on the host cores (the only other place this file runs it)."""
+    if rank != 0:
+        return
+    w = make_workload(args.workload, args.nb)
+    import oracle
+    H, W = w.gbuf.depth.shape
+    prob = oracle.Problem(w.gbuf, w.params, w.noise, w.sh)
+    per_px = 2 * w.params.num_slices * w.params.steps_per_side
+    n = 192  # pixels per step: a bounded sample so the whole run takes a few minutes
+    rng = np.random.default_rng(11)
+    times = []
+    for s in range(args.warmup + args.steps):
+        idx = rng.choice(H * W, size=n, replace=False)
+        xy = np.stack([idx % W, idx // W], 1).astype(np.int32)
+        t0 = time.perf_counter()
+        oracle.fp64(prob, xy)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = args.steps * n * per_px / total / 1e9
+    ms_frame = total / args.steps * (H * W / n) * 1e3
+    out = {"impl": "reference", "metric": "Gsamples/s (ms/frame at 4K)", "value": value, "unit": "Gsamples/s",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_frame,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": w.name, "sample_pixels_per_step": n},
+           "cpu_baseline": {"value": value, "unit": "Gsamples/s", "cores": 1, "kind": "oracle",
+                            "sample": f"FP64 oracle, 1 thread, {n} random pixels per step of the {W}x{H} frame"},
+           "e2e": {"value": value, "unit": "Gsamples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import torch
+
+    import paper_2301_11376_gb300 as ssilvb
+    ssilvb.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    w = make_workload(args.workload, args.nb)
+    H, W = w.gbuf.depth.shape
+    spf = samples_per_frame(w)
+    g = w.gbuf
+    d = torch.from_numpy(g.depth).to(dev)
+    n = torch.from_numpy(np.ascontiguousarray(g.normal)).to(dev)
+    r = torch.from_numpy(np.ascontiguousarray(g.radiance)).to(dev)
+    out0, out1, _ = ssilvb.alloc_outputs(H, W, w.params, dev)
+    ctx = ssilvb.Context(local)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
+
+    def step():
+        ctx.gather(d, n, r, g.camera, w.params, out0, out1, None, noise=w.noise, sh=w.sh, stream=stream)
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        step()
+    ctx.synchronize(stream)
+    torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))  # evict the G-buffer from L2 between timed steps (outside the events)
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    ctx.synchronize(stream)
+    kern_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    t_dev = sum(kern_ms) / 1e3
+    t_max = max_over_ranks(world, t_dev)
+    value = world * args.steps * spf / t_max / 1e9
+    ms = t_max / args.steps * 1e3
+
+    # e2e: the same gather through the host-buffer entry point (copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        hd, hn, hr = pin(g.depth), pin(g.normal), pin(g.radiance)
+        ho0 = torch.empty((H, W, 4), dtype=torch.float32).pin_memory()
+        ho1 = torch.empty((H, W, 4), dtype=torch.float32).pin_memory() if out1 is not None else None
+        for _ in range(2):
+            ctx.gather_host(hd, hn, hr, g.camera, w.params, ho0, ho1, None, noise=w.noise, sh=w.sh, stream=stream)
+        ke = max(3, min(args.steps, 10))
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            ctx.gather_host(hd, hn, hr, g.camera, w.params, ho0, ho1, None, noise=w.noise, sh=w.sh, stream=stream)
+        te = max_over_ranks(world, time.perf_counter() - t0)
+        h2d = hd.numel() * 4 + hn.numel() * hn.element_size() + hr.numel() * hr.element_size()
+        d2h = ho0.numel() * 4 + (ho1.numel() * 4 if ho1 is not None else 0)
+        e2e = {"value": world * ke * spf / te / 1e9, "unit": "Gsamples/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": te / ke * 1e3}
+
+    if rank != 0:
+        return
+    ops, counts = algorithmic_ops_per_frame(w)
+    peak_ops = SM_COUNT_GB300 * FP32_LANES_PER_SM * 2.070e9
+    achieved = ops / (ms / 1e3)
+    roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
+            "frac": achieved / peak_ops, "traffic": None,
+            "kernel": "gather_tile_kernel", "ops_per_launch": ops,
+            "ops_per_sample": ops / spf,
+            "peak_note": "152 SMs x 128 FP32 lanes x 2.070 GHz max SM clock (derived)"}
+    cpu = None if args.no_cpu_baseline else cpu_baseline(w)
+    out = {"metric": "Gsamples/s (ms/frame at 4K)", "value": value, "unit": "Gsamples/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": w.name, "samples_per_frame": spf, "l2": "flushed (256 MB write) between timed steps",
+                      "storage": "f32 depth, f16 normal+radiance" if w.gbuf.normal.dtype == np.float16 else "f32",
+                      "parallelism": f"replicas x{world}"},
+           "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": args.steps,
+           "kernel_ms": {"min": min(kern_ms), "median": statistics.median(kern_ms), "max": max(kern_ms)},
+           "wall_s_timed_region": wall}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,163 @@
+/*
+ * ssilvb: screen-space indirect lighting with a visibility bitmask, on GB300.
+ *
+ * C ABI of the GPU gather of Therrien, Levesque and Gilet, "Screen Space
+ * Indirect Lighting with Visibility Bitmask" (arXiv 2301.11376).  For every
+ * pixel and every slice direction around the view vector the gather marches
+ * depth samples on both sides, turns each sample's front and back elevation
+ * (the back one from a constant thickness t) into a run of sectors of an
+ * N_b-bit visibility mask, adds the newly occluded sectors' share of the
+ * sample's direct radiance into indirect diffuse light, and ORs the run into
+ * the slice mask, which gives ambient occlusion and the directionally
+ * occluded ambient light (Algorithm 1 of Section 3.1; Sections 3.2 and 3.3).
+ *
+ * Conventions shared by every entry point
+ *   - Plain pointers and sizes only.  Device pointers are CUDA device memory
+ *     on the context's device; "host" pointers are ordinary CPU memory.
+ *   - Every argument is validated before anything is enqueued; on any error
+ *     nothing is launched and the call returns a status != SSILVB_OK, with a
+ *     human-readable detail in ssilvb_last_error().
+ *   - Calls that take a stream are asynchronous on that stream (a
+ *     cudaStream_t; NULL = the legacy default stream) unless stated otherwise.
+ *   - The caller owns every buffer it passes.  The library keeps no pointer
+ *     to them after the work enqueued by the call has finished.
+ *   - A context is not thread-safe: use one per host thread.  No C++
+ *     exception crosses this boundary.
+ *
+ * Geometry conventions
+ *   View space is right-handed, camera at the origin looking along -z, +y up.
+ *   Image rows go down.  The centre of pixel (x, y) is (x + 0.5, y + 0.5) and
+ *   projects from view position P as u = cx + fx * P.x / (-P.z),
+ *   v = cy - fy * P.y / (-P.z).  Depth is linear: z = -P.z > 0.  A depth value
+ *   that is not in (0, +INF) (including +INF and NaN) marks sky: such pixels
+ *   output AO = 1, GI = 0, ambient = 0 and are never used as samples.
+ */
+#ifndef SSILVB_H
+#define SSILVB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st; /* cudaStream_t is struct CUstream_st* */
+
+typedef struct ssilvb_ctx ssilvb_ctx; /* opaque, owned by the library */
+
+typedef enum {
+    SSILVB_OK = 0,
+    SSILVB_ERR_INVALID_ARG = 1,   /* null pointer, bad size, alignment or pitch, parameter out of range */
+    SSILVB_ERR_UNSUPPORTED = 2,   /* valid request this build does not implement (e.g. N_b = 128) */
+    SSILVB_ERR_OUT_OF_MEMORY = 3, /* a context allocation failed */
+    SSILVB_ERR_CUDA = 4,          /* a CUDA runtime or driver call failed; see ssilvb_last_error */
+    SSILVB_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up */
+    SSILVB_ERR_DEVICE_CHECK = 6   /* a device-side consistency check failed */
+} ssilvb_status;
+
+/* Storage of the normal and radiance planes: 4 components per pixel
+ * (xyz / rgb, the 4th ignored), 32-bit float or IEEE binary16. */
+typedef enum { SSILVB_FMT_F32X4 = 0, SSILVB_FMT_F16X4 = 1 } ssilvb_format;
+
+/* The G-buffer the gather reads (Algorithm 1 inputs p, n_p and the light buffer of
+ * Section 3.3: depth, view-space normals and direct radiance "with shadows").
+ * Device pointers, row-major with a row pitch in BYTES; base pointers 16-byte
+ * aligned; depth pitch a multiple of 4, normal/radiance pitch a multiple of the
+ * pixel size (16 for F32X4, 8 for F16X4).  normal_fmt must equal radiance_fmt. */
+typedef struct {
+    int width, height;            /* 1 .. 16384 each */
+    const float *depth;           /* [height][pitch] linear view depth */
+    size_t depth_pitch;
+    const void *normal;           /* view-space unit normal, xyz used */
+    size_t normal_pitch;
+    int normal_fmt;               /* ssilvb_format */
+    const void *radiance;         /* direct radiance, rgb used */
+    size_t radiance_pitch;
+    int radiance_fmt;             /* ssilvb_format */
+} ssilvb_gbuffer;
+
+/* Pinhole intrinsics in pixels (fx, fy > 0) and the row-major view->world
+ * rotation, used only to look up the ambient environment in world space. */
+typedef struct {
+    float fx, fy, cx, cy;
+    float view_to_world[9];
+} ssilvb_camera;
+
+/* Parameters of the method (Algorithm 1; Sections 3.1-3.3, 4.1-4.3). */
+typedef struct {
+    int num_slices;        /* N_d, 1..16: slice directions per pixel, azimuth (i + xi_phi) pi / N_d */
+    int steps_per_side;    /* N_s, 1..64: samples on each side of the slice */
+    float radius;          /* R > 0 (view-space units): projected radius r = R fx / z pixels */
+    float thickness;       /* t > 0; +INF = infinite thickness (horizon-based occlusion) */
+    float thickness_slope; /* k_t >= 0: thickness grows linearly with depth, t(z) = t + k_t z */
+    int sector_count;      /* N_b: 32 or 64 */
+    int hit_rule;          /* 0: a sector is occluded when at least half covered (Section 3.1);
+                              1: floor/ceil run of Algorithm 1 */
+    int step_mode;         /* 0: constant steps r (j+1+xi_s)/(N_s+1);
+                              1: quadratic ("exponential") steps r ((j+1+xi_s)/(N_s+1))^2 */
+    int ambient_cones;     /* N_a in {0, 1, 2, 4, 8} dividing N_b: ambient cones per slice, 0 = off */
+    int compute_gi;        /* 1 = indirect diffuse (reads normal and radiance at samples), 0 = off */
+    const float *noise_table; /* HOST, 16 x (xi_phi, xi_s) in [0,1), row (y&3)*4 + (x&3); NULL = zeros */
+    const float *sh_rgb;   /* HOST, 9 x 3 real SH radiance coefficients [m][rgb] of the ambient
+                              environment (order Y00, Y1-1, Y10, Y11, Y2-2, Y2-1, Y20, Y21, Y22);
+                              required iff ambient_cones > 0 */
+} ssilvb_params;
+
+/* Outputs, device pointers.  out0 (required): float4 per pixel = (GI.r, GI.g, GI.b, AO),
+ * AO = mean over slices of the unoccluded sector fraction (1 = fully visible).
+ * out1 (required iff ambient_cones > 0): float4 = (ambient.r, .g, .b, 0).
+ * Pitches in bytes, multiples of 16; bases 16-byte aligned.
+ * masks (optional, NULL = not written): the final slice bitmasks, dense
+ * [num_slices][height][width] of uint32 (N_b = 32) or uint64 (N_b = 64), 8-byte aligned. */
+typedef struct {
+    float *out0;
+    size_t out0_pitch;
+    float *out1;
+    size_t out1_pitch;
+    void *masks;
+} ssilvb_output;
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int ssilvb_version(void);
+
+/* Human-readable name of a status code (static storage). */
+const char *ssilvb_status_string(ssilvb_status s);
+
+/* Detail of the context's last failure ("" if none); valid until the next call on ctx.
+ * NULL ctx returns the detail of the last failed ssilvb_create in this thread. */
+const char *ssilvb_last_error(const ssilvb_ctx *ctx);
+
+/* Create a context on CUDA device cuda_device.  *out_ctx receives the context,
+ * or NULL on failure.  Allocates a device status word; errors:
+ * INVALID_ARG (null out_ctx, bad device), CUDA, OUT_OF_MEMORY. */
+ssilvb_status ssilvb_create(ssilvb_ctx **out_ctx, int cuda_device);
+
+/* Destroy a context and free what it owns (NULL is allowed).  Synchronises the device. */
+ssilvb_status ssilvb_destroy(ssilvb_ctx *ctx);
+
+/* The visibility-bitmask gather over one frame (Algorithm 1 per pixel, with the
+ * ambient cones of Section 3.2 and indirect diffuse of Section 3.3).  All G-buffer
+ * and output pointers are device memory; host pointers inside params are read
+ * during the call only.  Enqueues the work on stream and returns. */
+ssilvb_status ssilvb_gather(ssilvb_ctx *ctx, const ssilvb_gbuffer *gbuffer, const ssilvb_camera *camera,
+                            const ssilvb_params *params, const ssilvb_output *out, struct CUstream_st *stream);
+
+/* The same gather on HOST buffers: gbuffer and out point to host memory (pinned
+ * memory gives the fastest copies).  The context stages the frame in device
+ * buffers it owns (grown on demand and kept for reuse), copies the inputs host to
+ * device, runs the gather and copies the outputs back, all on stream, and returns
+ * after the outputs are in host memory (the call synchronises stream). */
+ssilvb_status ssilvb_gather_host(ssilvb_ctx *ctx, const ssilvb_gbuffer *gbuffer, const ssilvb_camera *camera,
+                                 const ssilvb_params *params, const ssilvb_output *out,
+                                 struct CUstream_st *stream);
+
+/* Wait for the work enqueued on stream and report a failure of it: CUDA
+ * (asynchronous launch or execution error) or DEVICE_CHECK / TIMEOUT from the
+ * context's device status word, which the call then clears. */
+ssilvb_status ssilvb_synchronize(ssilvb_ctx *ctx, struct CUstream_st *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SSILVB_H */

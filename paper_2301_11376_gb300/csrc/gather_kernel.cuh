@@ -1,0 +1,320 @@
+// Visibility-bitmask gather kernel for sm_103a (GB300).
+//
+// Per pixel: Algorithm 1 of Therrien, Levesque, Gilet, "Screen Space Indirect
+// Lighting with Visibility Bitmask" (Section 3.1), the directionally occluded
+// ambient cones of Section 3.2 and the indirect diffuse term of Section 3.3.
+//
+// The binary32 operation sequence on the bitmask path is fixed: round to
+// nearest even, fused multiply-adds only where fmaf() is written (the file is
+// built with -fmad=false), IEEE sqrt, no flush to zero.  Integer decisions
+// taken from floating point (which pixel a step reads, which sectors a sample
+// covers) are therefore reproducible bit for bit on any IEEE machine.
+//
+// Readings of the paper used here:
+//   - slices i = 0..N_d-1 at azimuth (i + xi_phi) pi / N_d; steps j = 0..N_s-1
+//     on each side at offset r (j+1+xi_s)/(N_s+1) (or its square for the
+//     quadratic step mode), side -omega first, near to far;
+//   - the back sample lies behind the front one along the centre pixel's view
+//     ray, s_b = s_f + t p/|p| (Figure 4);
+//   - elevation h = sigma acos(l.v/|l|), sector coordinate
+//     X = (h - gamma) N_b/pi + N_b/2 clamped to [0, N_b], gamma the signed angle
+//     of the projected normal (Eq. 4: the bit field is centred on it);
+//   - a sector is occluded when at least half covered (round criterion), i.e.
+//     the sectors whose centres lie in [A, B] when B - A >= 1/2, set at once;
+//   - GI weight (newly occluded sectors / N_b) max(0, n_p.l) max(0, -n_j.l).
+#pragma once
+
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace ssilvb {
+
+constexpr int kMaxSlices = 16;
+constexpr int kMaxCones = 8;
+
+// Everything a launch needs, passed by value as a __grid_constant__ parameter.
+struct GatherParams {
+    const float *depth;
+    const char *normal;
+    const char *radiance;
+    float *out0;
+    float *out1;
+    void *masks;
+    size_t depth_pitch;    // elements (floats)
+    size_t normal_pitch;   // bytes
+    size_t radiance_pitch; // bytes
+    size_t out0_pitch;     // elements (floats)
+    size_t out1_pitch;     // elements (floats)
+    int W, H;
+    int nd, ns, na;
+    int hit_rule, step_mode, gi;
+    // per-launch binary32 constants
+    float inv_fx, inv_fy, kx0, ninv_fy, ky0;
+    float Rfx, dn, K, half_nb, f_nb, inv_nb, inv_nd;
+    float t0, kt;
+    float xi_s[16];
+    float dcos[16][kMaxSlices];
+    float dsin[16][kMaxSlices];
+    float ccos[kMaxCones], csin[kMaxCones];
+    float R[9];
+    float sh[27];
+    float Y0, Y1, Y2, Y3, Y4;
+};
+
+// Abramowitz and Stegun 4.4.46: acos(x) = sqrt(1 - x) (a0 + a1 x + ... + a7 x^7), 0 <= x <= 1.
+__device__ __forceinline__ float own_acos(float c) {
+    const float a = fabsf(c);
+    const float s = sqrtf(1.0f - a);
+    float P = fmaf(-0.0012624911f, a, 0.0066700901f);
+    P = fmaf(P, a, -0.0170881256f);
+    P = fmaf(P, a, 0.0308918810f);
+    P = fmaf(P, a, -0.0501743046f);
+    P = fmaf(P, a, 0.0889789874f);
+    P = fmaf(P, a, -0.2145988016f);
+    P = fmaf(P, a, 1.5707963050f);
+    const float r = s * P;
+    return c < 0.0f ? 3.14159265358979323846f - r : r;
+}
+
+// Reciprocal square root: integer seed 0x5f3759df - (bits >> 1) (Lomont 2003), then
+// three Newton steps y <- y (1.5 - 0.5 x y^2).  Branch-free; reproducible on any IEEE FPU.
+__device__ __forceinline__ float own_rsqrt(float x) {
+    x = fmaxf(x, 1.17549435e-38f);
+    float y = __uint_as_float(0x5f3759dfu - (__float_as_uint(x) >> 1));
+    const float hx = 0.5f * x;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float t = y * y;
+        const float u = fmaf(-hx, t, 1.5f);
+        y = y * u;
+    }
+    return y;
+}
+
+__device__ __forceinline__ float clamp1(float c) { return fmaxf(fminf(c, 1.0f), -1.0f); }
+
+// 1.5 * 2^23: adding it to |v| < 2^22 leaves round(v) in the low mantissa bits.
+constexpr float kMagic = 12582912.0f;
+constexpr int kMagicBits = 0x4B400000;
+
+// Bits [lo, lo + cnt) of a 32-bit word (0 when lo >= 32 or cnt == 0).
+__device__ __forceinline__ uint32_t run32(int lo, int cnt) {
+    uint32_t r;
+    asm("bmsk.clamp.b32 %0, %1, %2;" : "=r"(r) : "r"(lo), "r"(cnt));
+    return r;
+}
+
+template <int NB> struct MaskT;
+template <> struct MaskT<32> { using T = uint32_t; };
+template <> struct MaskT<64> { using T = unsigned long long; };
+
+template <int NB> __device__ __forceinline__ typename MaskT<NB>::T run_mask(int lo, int hi);
+template <> __device__ __forceinline__ uint32_t run_mask<32>(int lo, int hi) { return run32(lo, hi - lo); }
+template <> __device__ __forceinline__ unsigned long long run_mask<64>(int lo, int hi) {
+    const int a0 = min(lo, 32), e0 = min(hi, 32);
+    const int a1 = max(lo - 32, 0), e1 = max(hi - 32, 0);
+    const uint32_t w0 = run32(a0, max(e0 - a0, 0));
+    const uint32_t w1 = run32(a1, max(e1 - a1, 0));
+    return ((unsigned long long)w1 << 32) | w0;
+}
+
+__device__ __forceinline__ int popc_(uint32_t v) { return __popc(v); }
+__device__ __forceinline__ int popc_(unsigned long long v) { return __popcll(v); }
+
+// Sector run of a sample with endpoints A <= B (sector units, already in [0, N_b]).
+template <int NB>
+__device__ __forceinline__ typename MaskT<NB>::T sector_run(float A, float B, int hit_rule) {
+    int lo, hi;
+    if (hit_rule == 0) {
+        // ceil(A - 1/2) and floor(B + 1/2), exact through a directed-rounding add of 1.5*2^23
+        lo = __float_as_int(__fadd_ru(A - 0.5f, kMagic)) - kMagicBits;
+        hi = __float_as_int(__fadd_rd(B + 0.5f, kMagic)) - kMagicBits;
+        if (!(B - A >= 0.5f)) hi = lo;
+    } else {
+        lo = __float_as_int(__fadd_rd(A, kMagic)) - kMagicBits;
+        hi = min(lo + (__float_as_int(__fadd_ru(B - A, kMagic)) - kMagicBits), NB);
+    }
+    hi = max(hi, lo);
+    return run_mask<NB>(lo, hi);
+}
+
+template <bool F16>
+__device__ __forceinline__ float3 load_xyz(const char *base, size_t pitch, int x, int y) {
+    const char *row = base + (size_t)y * pitch;
+    if (F16) {
+        const uint2 v = __ldg(reinterpret_cast<const uint2 *>(row) + x);
+        const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&v.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&v.y));
+        return make_float3(a.x, a.y, b.x);
+    } else {
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(row) + x);
+        return make_float3(v.x, v.y, v.z);
+    }
+}
+
+__device__ __forceinline__ bool is_geometry(float z) { return z > 0.0f && z < __int_as_float(0x7f800000); }
+
+// The whole per-pixel gather.  cls is the pixel's 4x4 noise class (y & 3) * 4 + (x & 3).
+template <int NB, bool F16, bool INF_T>
+__device__ __forceinline__ void gather_pixel(const GatherParams &P, int x, int y) {
+    using M = typename MaskT<NB>::T;
+    const float z = __ldg(P.depth + (size_t)y * P.depth_pitch + x);
+    float4 *o0 = reinterpret_cast<float4 *>(P.out0 + (size_t)y * P.out0_pitch) + x;
+    if (!is_geometry(z)) {
+        *o0 = make_float4(0.0f, 0.0f, 0.0f, 1.0f);
+        if (P.na > 0) *(reinterpret_cast<float4 *>(P.out1 + (size_t)y * P.out1_pitch) + x) = make_float4(0, 0, 0, 0);
+        if (P.masks)
+            for (int i = 0; i < P.nd; ++i) reinterpret_cast<M *>(P.masks)[((size_t)i * P.H + y) * P.W + x] = 0;
+        return;
+    }
+
+    // Pixel setup (Algorithm 1: p, n_p, projected radius, step size).
+    const float u = (float)x + 0.5f, v = (float)y + 0.5f;
+    const float ax = fmaf(u, P.inv_fx, P.kx0), by = fmaf(v, P.ninv_fy, P.ky0);
+    const float px = ax * z, py = by * z;
+    const float rd = own_rsqrt(fmaf(ax, ax, fmaf(by, by, 1.0f)));
+    const float vx = -(ax * rd), vy = -(by * rd), vz = rd;
+    const float3 n = load_xyz<F16>(P.normal, P.normal_pitch, x, y);
+    const float rpx = fminf(P.Rfx / z, 1048576.0f);
+    const int cls = (y & 3) * 4 + (x & 3);
+    const float xidn = P.xi_s[cls] * P.dn;
+    float tp = 0.0f, t2 = 0.0f, m2t = 0.0f;
+    if (!INF_T) {
+        tp = fmaf(P.kt, z, P.t0);
+        t2 = tp * tp;
+        m2t = -2.0f * tp;
+    }
+
+    float AO = 0.0f, GIr = 0.0f, GIg = 0.0f, GIb = 0.0f, AMr = 0.0f, AMg = 0.0f, AMb = 0.0f;
+    for (int i = 0; i < P.nd; ++i) {
+        const float cphi = P.dcos[cls][i], sphi = P.dsin[cls][i];
+        // Slice plane: s = normalize(w3 - (w3.v) v), w3 the view-space image of omega.
+        const float w3x = cphi * P.inv_fx, w3y = -(sphi * P.inv_fy);
+        const float wv = fmaf(w3x, vx, w3y * vy);
+        const float sx0 = fmaf(-wv, vx, w3x), sy0 = fmaf(-wv, vy, w3y), sz0 = -(wv * vz);
+        const float rs = own_rsqrt(fmaf(sx0, sx0, fmaf(sy0, sy0, sz0 * sz0)));
+        const float sx = sx0 * rs, sy = sy0 * rs, sz = sz0 * rs;
+        // Projected normal angle gamma (sector frame centred on it, Eq. 4).
+        const float nv = fmaf(n.x, vx, fmaf(n.y, vy, n.z * vz));
+        const float nsd = fmaf(n.x, sx, fmaf(n.y, sy, n.z * sz));
+        const float pn2 = fmaf(nv, nv, nsd * nsd);
+        float cg = 1.0f, sg = 0.0f, gam = 0.0f;
+        if (pn2 > 0.0f) {
+            const float rpn = own_rsqrt(pn2);
+            cg = nv * rpn;
+            sg = nsd * rpn;
+            gam = own_acos(clamp1(cg));
+            if (nsd < 0.0f) gam = -gam;
+        }
+        const float off = fmaf(-gam, P.K, P.half_nb);
+
+        M b = 0;
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            const bool pos = side == 1;
+            const float wsx = pos ? cphi : -cphi, wsy = pos ? sphi : -sphi;
+            const float sK = pos ? P.K : -P.K;
+            const float edge = pos ? P.f_nb : 0.0f;
+#pragma unroll 2
+            for (int j = 0; j < P.ns; ++j) {
+                const float uj = fmaf((float)(j + 1), P.dn, xidn);
+                const float o = P.step_mode == 0 ? uj * rpx : (uj * uj) * rpx;
+                const float rx = o * wsx + kMagic, ry = o * wsy + kMagic;
+                const int dx = __float_as_int(rx) - kMagicBits, dy = __float_as_int(ry) - kMagicBits;
+                if ((dx | dy) == 0) continue;
+                const int qx = x + dx, qy = y + dy;
+                if ((unsigned)qx >= (unsigned)P.W || (unsigned)qy >= (unsigned)P.H) continue;
+                const float zq = __ldg(P.depth + (size_t)qy * P.depth_pitch + qx);
+                if (!is_geometry(zq)) continue;
+
+                // Front sample.
+                const float uq = u + (rx - kMagic), vq = v + (ry - kMagic);
+                const float aq = fmaf(uq, P.inv_fx, P.kx0), bq = fmaf(vq, P.ninv_fy, P.ky0);
+                const float lx = fmaf(aq, zq, -px), ly = fmaf(bq, zq, -py), lz = z - zq;
+                const float dv = fmaf(lx, vx, fmaf(ly, vy, lz * vz));
+                const float ll = fmaf(lx, lx, fmaf(ly, ly, lz * lz));
+                const float rl = own_rsqrt(ll);
+                const float Xf = fminf(fmaxf(fmaf(own_acos(clamp1(dv * rl)), sK, off), 0.0f), P.f_nb);
+                // Back sample, thickness t behind the front one.
+                float Xb;
+                if (INF_T) {
+                    Xb = edge;
+                } else {
+                    const float dvb = dv - tp;
+                    const float llb = fmaf(m2t, dv, ll + t2);
+                    const float cb = clamp1(dvb * own_rsqrt(llb));
+                    Xb = fminf(fmaxf(fmaf(own_acos(cb), sK, off), 0.0f), P.f_nb);
+                }
+                const float A = fminf(Xf, Xb), B = fmaxf(Xf, Xb);
+                const M bj = sector_run<NB>(A, B, P.hit_rule);
+                const int newly = popc_(bj & ~b);
+                b |= bj;
+
+                // Indirect light of the newly occluded sectors (Section 3.3).
+                if (newly > 0 && P.gi) {
+                    const float3 cj = load_xyz<F16>(P.radiance, P.radiance_pitch, qx, qy);
+                    const float3 nj = load_xyz<F16>(P.normal, P.normal_pitch, qx, qy);
+                    const float cp = fmaxf(fmaf(n.x, lx, fmaf(n.y, ly, n.z * lz)) * rl, 0.0f);
+                    const float cq = fmaxf(-(fmaf(nj.x, lx, fmaf(nj.y, ly, nj.z * lz)) * rl), 0.0f);
+                    const float wgt = (((float)newly * P.inv_nb) * cp) * cq;
+                    GIr = fmaf(wgt, cj.x, GIr);
+                    GIg = fmaf(wgt, cj.y, GIg);
+                    GIb = fmaf(wgt, cj.z, GIb);
+                }
+            }
+        }
+
+        // Slice end: unoccluded fraction, then the ambient cones (Section 3.2).
+        AO += (float)(NB - popc_(b)) * P.inv_nb;
+        if (P.na > 0) {
+            const int g = NB / P.na;
+            for (int k = 0; k < P.na; ++k) {
+                const M Mk = run_mask<NB>(k * g, (k + 1) * g);
+                const int freek = popc_(~b & Mk);
+                const float ck = fmaf(cg, P.ccos[k], -(sg * P.csin[k]));
+                const float sk = fmaf(sg, P.ccos[k], cg * P.csin[k]);
+                const float a3x = fmaf(ck, vx, sk * sx), a3y = fmaf(ck, vy, sk * sy), a3z = fmaf(ck, vz, sk * sz);
+                const float wx = fmaf(P.R[0], a3x, fmaf(P.R[1], a3y, P.R[2] * a3z));
+                const float wy = fmaf(P.R[3], a3x, fmaf(P.R[4], a3y, P.R[5] * a3z));
+                const float wz = fmaf(P.R[6], a3x, fmaf(P.R[7], a3y, P.R[8] * a3z));
+                float Y[9];
+                Y[0] = P.Y0;
+                Y[1] = P.Y1 * wy;
+                Y[2] = P.Y1 * wz;
+                Y[3] = P.Y1 * wx;
+                Y[4] = P.Y2 * (wx * wy);
+                Y[5] = P.Y2 * (wy * wz);
+                Y[6] = P.Y3 * fmaf(3.0f * wz, wz, -1.0f);
+                Y[7] = P.Y2 * (wx * wz);
+                Y[8] = P.Y4 * fmaf(wx, wx, -(wy * wy));
+                const float wt = (float)freek * P.inv_nb;
+                float L0 = P.sh[0] * Y[0], L1 = P.sh[1] * Y[0], L2 = P.sh[2] * Y[0];
+#pragma unroll
+                for (int m = 1; m < 9; ++m) {
+                    L0 = fmaf(P.sh[3 * m + 0], Y[m], L0);
+                    L1 = fmaf(P.sh[3 * m + 1], Y[m], L1);
+                    L2 = fmaf(P.sh[3 * m + 2], Y[m], L2);
+                }
+                AMr = fmaf(wt, L0, AMr);
+                AMg = fmaf(wt, L1, AMg);
+                AMb = fmaf(wt, L2, AMb);
+            }
+        }
+        if (P.masks) reinterpret_cast<M *>(P.masks)[((size_t)i * P.H + y) * P.W + x] = b;
+    }
+    *o0 = make_float4(GIr * P.inv_nd, GIg * P.inv_nd, GIb * P.inv_nd, AO * P.inv_nd);
+    if (P.na > 0)
+        *(reinterpret_cast<float4 *>(P.out1 + (size_t)y * P.out1_pitch) + x) =
+            make_float4(AMr * P.inv_nd, AMg * P.inv_nd, AMb * P.inv_nd, 0.0f);
+}
+
+// One thread per pixel, 32 x 8 pixel tiles.
+template <int NB, bool F16, bool INF_T>
+__global__ void __launch_bounds__(256) gather_tile_kernel(const __grid_constant__ GatherParams P) {
+    const int x = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
+    if (x >= P.W || y >= P.H) return;
+    gather_pixel<NB, F16, INF_T>(P, x, y);
+}
+
+}  // namespace ssilvb

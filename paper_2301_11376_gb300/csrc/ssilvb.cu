@@ -1,0 +1,378 @@
+// Host side of the ssilvb C ABI: argument validation, per-launch constants and
+// kernel launches for the visibility-bitmask gather (arXiv 2301.11376,
+// Algorithm 1, Sections 3.1-3.3).  The declarations and their contracts are in
+// include/ssilvb.h.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "gather_kernel.cuh"
+#include "ssilvb.h"
+
+#define SSILVB_VERSION 10000
+
+struct ssilvb_ctx {
+    int device = 0;
+    int num_sms = 0;
+    int *d_status = nullptr;   // device status word (device-side checks and bounded waits)
+    std::string last_error;
+    // staging for ssilvb_gather_host
+    void *stage = nullptr;
+    size_t stage_bytes = 0;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+ssilvb_status fail(ssilvb_ctx *ctx, ssilvb_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (ctx) ctx->last_error = buf;
+    else g_create_error = buf;
+    return s;
+}
+
+ssilvb_status cuda_fail(ssilvb_ctx *ctx, cudaError_t e, const char *what) {
+    return fail(ctx, SSILVB_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+ssilvb_status validate(ssilvb_ctx *ctx, const ssilvb_gbuffer *g, const ssilvb_camera *c, const ssilvb_params *p,
+                       const ssilvb_output *o, bool device_ptrs) {
+    if (!g || !c || !p || !o) return fail(ctx, SSILVB_ERR_INVALID_ARG, "null gbuffer, camera, params or output");
+    if (g->width < 1 || g->height < 1 || g->width > 16384 || g->height > 16384)
+        return fail(ctx, SSILVB_ERR_INVALID_ARG, "image size %dx%d outside 1..16384", g->width, g->height);
+    if (!g->depth || !g->normal || !g->radiance) return fail(ctx, SSILVB_ERR_INVALID_ARG, "null G-buffer plane");
+    if (g->normal_fmt != SSILVB_FMT_F32X4 && g->normal_fmt != SSILVB_FMT_F16X4)
+        return fail(ctx, SSILVB_ERR_INVALID_ARG, "unknown normal format %d", g->normal_fmt);
+    if (g->radiance_fmt != SSILVB_FMT_F32X4 && g->radiance_fmt != SSILVB_FMT_F16X4)
+        return fail(ctx, SSILVB_ERR_INVALID_ARG, "unknown radiance format %d", g->radiance_fmt);
+    if (g->normal_fmt != g->radiance_fmt)
+        return fail(ctx, SSILVB_ERR_UNSUPPORTED, "normal and radiance formats must match");
+    const size_t px = g->normal_fmt == SSILVB_FMT_F16X4 ? 8 : 16;
+    const size_t W = (size_t)g->width;
+    if (g->depth_pitch < W * 4 || g->depth_pitch % 4)
+        return fail(ctx, SSILVB_ERR_INVALID_ARG, "depth pitch %zu invalid for width %zu", g->depth_pitch, W);
+    if (g->normal_pitch < W * px || g->normal_pitch % px || g->radiance_pitch < W * px || g->radiance_pitch % px)
+        return fail(ctx, SSILVB_ERR_INVALID_ARG, "normal/radiance pitch invalid (pixel size %zu)", px);
+    if (!aligned(g->depth, 16) || !aligned(g->normal, 16) || !aligned(g->radiance, 16))
+        return fail(ctx, SSILVB_ERR_INVALID_ARG, "G-buffer planes must be 16-byte aligned");
+    if (!(c->fx > 0.0f) || !(c->fy > 0.0f) || !std::isfinite(c->fx) || !std::isfinite(c->fy) ||
+        !std::isfinite(c->cx) || !std::isfinite(c->cy))
+        return fail(ctx, SSILVB_ERR_INVALID_ARG, "camera intrinsics must be finite with fx, fy > 0");
+    for (int i = 0; i < 9; ++i)
+        if (!std::isfinite(c->view_to_world[i])) return fail(ctx, SSILVB_ERR_INVALID_ARG, "view_to_world not finite");
+    if (p->num_slices < 1 || p->num_slices > ssilvb::kMaxSlices)
+        return fail(ctx, SSILVB_ERR_INVALID_ARG, "num_slices %d outside 1..16", p->num_slices);
+    if (p->steps_per_side < 1 || p->steps_per_side > 64)
+        return fail(ctx, SSILVB_ERR_INVALID_ARG, "steps_per_side %d outside 1..64", p->steps_per_side);
+    if (!(p->radius > 0.0f) || !std::isfinite(p->radius))
+        return fail(ctx, SSILVB_ERR_INVALID_ARG, "radius must be finite and > 0");
+    if (!(p->thickness > 0.0f)) return fail(ctx, SSILVB_ERR_INVALID_ARG, "thickness must be > 0 (+INF allowed)");
+    if (!(p->thickness_slope >= 0.0f) || !std::isfinite(p->thickness_slope))
+        return fail(ctx, SSILVB_ERR_INVALID_ARG, "thickness_slope must be finite and >= 0");
+    if (p->sector_count == 128) return fail(ctx, SSILVB_ERR_UNSUPPORTED, "sector_count 128 is not built");
+    if (p->sector_count != 32 && p->sector_count != 64)
+        return fail(ctx, SSILVB_ERR_INVALID_ARG, "sector_count %d not in {32, 64}", p->sector_count);
+    if (p->hit_rule != 0 && p->hit_rule != 1) return fail(ctx, SSILVB_ERR_INVALID_ARG, "hit_rule must be 0 or 1");
+    if (p->step_mode != 0 && p->step_mode != 1) return fail(ctx, SSILVB_ERR_INVALID_ARG, "step_mode must be 0 or 1");
+    if (p->compute_gi != 0 && p->compute_gi != 1) return fail(ctx, SSILVB_ERR_INVALID_ARG, "compute_gi must be 0 or 1");
+    const int na = p->ambient_cones;
+    if (na != 0 && na != 1 && na != 2 && na != 4 && na != 8)
+        return fail(ctx, SSILVB_ERR_INVALID_ARG, "ambient_cones %d not in {0,1,2,4,8}", na);
+    if (na > 0 && !p->sh_rgb) return fail(ctx, SSILVB_ERR_INVALID_ARG, "sh_rgb required when ambient_cones > 0");
+    if (p->noise_table)
+        for (int i = 0; i < 32; ++i)
+            if (!(p->noise_table[i] >= 0.0f && p->noise_table[i] < 1.0f))
+                return fail(ctx, SSILVB_ERR_INVALID_ARG, "noise_table[%d] not in [0, 1)", i);
+    if (p->sh_rgb && na > 0)
+        for (int i = 0; i < 27; ++i)
+            if (!std::isfinite(p->sh_rgb[i])) return fail(ctx, SSILVB_ERR_INVALID_ARG, "sh_rgb not finite");
+    if (!o->out0) return fail(ctx, SSILVB_ERR_INVALID_ARG, "out0 is required");
+    if (o->out0_pitch < W * 16 || o->out0_pitch % 16 || !aligned(o->out0, 16))
+        return fail(ctx, SSILVB_ERR_INVALID_ARG, "out0 must be 16-byte aligned with pitch >= 16*width, multiple of 16");
+    if (na > 0 && (!o->out1 || o->out1_pitch < W * 16 || o->out1_pitch % 16 || !aligned(o->out1, 16)))
+        return fail(ctx, SSILVB_ERR_INVALID_ARG, "out1 (16-byte aligned, pitch >= 16*width) required with ambient cones");
+    if (o->masks && !aligned(o->masks, 8)) return fail(ctx, SSILVB_ERR_INVALID_ARG, "masks must be 8-byte aligned");
+    if (device_ptrs) {
+        const void *ptrs[] = {g->depth, g->normal, g->radiance, o->out0, na > 0 ? o->out1 : nullptr, o->masks};
+        for (const void *q : ptrs) {
+            if (!q) continue;
+            cudaPointerAttributes a;
+            cudaError_t e = cudaPointerGetAttributes(&a, q);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return fail(ctx, SSILVB_ERR_INVALID_ARG, "pointer %p is not CUDA memory", q);
+            }
+            if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+                return fail(ctx, SSILVB_ERR_INVALID_ARG, "pointer %p is not device memory", q);
+            if (a.device != ctx->device)
+                return fail(ctx, SSILVB_ERR_INVALID_ARG, "pointer %p is on device %d, context on %d", q, a.device,
+                            ctx->device);
+        }
+    }
+    return SSILVB_OK;
+}
+
+// Per-launch constants.  Every expression is written out exactly as the method's binary32
+// specification fixes it (the same expressions any other IEEE implementation evaluates).
+void fill_params(ssilvb::GatherParams &P, const ssilvb_gbuffer *g, const ssilvb_camera *c, const ssilvb_params *p,
+                 const ssilvb_output *o) {
+    std::memset(&P, 0, sizeof(P));
+    P.depth = g->depth;
+    P.normal = static_cast<const char *>(g->normal);
+    P.radiance = static_cast<const char *>(g->radiance);
+    P.out0 = o->out0;
+    P.out1 = p->ambient_cones > 0 ? o->out1 : nullptr;
+    P.masks = o->masks;
+    P.depth_pitch = g->depth_pitch / 4;
+    P.normal_pitch = g->normal_pitch;
+    P.radiance_pitch = g->radiance_pitch;
+    P.out0_pitch = o->out0_pitch / 4;
+    P.out1_pitch = p->ambient_cones > 0 ? o->out1_pitch / 4 : 0;
+    P.W = g->width;
+    P.H = g->height;
+    P.nd = p->num_slices;
+    P.ns = p->steps_per_side;
+    P.na = p->ambient_cones;
+    P.hit_rule = p->hit_rule;
+    P.step_mode = p->step_mode;
+    P.gi = p->compute_gi;
+    const int nb = p->sector_count, nd = p->num_slices, ns = p->steps_per_side, na = p->ambient_cones;
+    P.inv_fx = 1.0f / c->fx;
+    P.inv_fy = 1.0f / c->fy;
+    P.kx0 = -(c->cx * P.inv_fx);
+    P.ninv_fy = -P.inv_fy;
+    P.ky0 = c->cy * P.inv_fy;
+    P.Rfx = p->radius * c->fx;
+    P.dn = 1.0f / (float)(ns + 1);
+    P.K = (float)((double)nb / M_PI);
+    P.half_nb = 0.5f * (float)nb;
+    P.f_nb = (float)nb;
+    P.inv_nb = 1.0f / (float)nb;
+    P.inv_nd = 1.0f / (float)nd;
+    P.t0 = p->thickness;
+    P.kt = p->thickness_slope;
+    for (int cl = 0; cl < 16; ++cl) {
+        const float xi_phi = p->noise_table ? p->noise_table[2 * cl] : 0.0f;
+        P.xi_s[cl] = p->noise_table ? p->noise_table[2 * cl + 1] : 0.0f;
+        for (int i = 0; i < nd; ++i) {
+            const double phi = ((double)i + (double)xi_phi) * M_PI / (double)nd;
+            P.dcos[cl][i] = (float)std::cos(phi);
+            P.dsin[cl][i] = (float)std::sin(phi);
+        }
+    }
+    for (int k = 0; k < na; ++k) {
+        const double th = -0.5 * M_PI + (k + 0.5) * M_PI / na;
+        P.ccos[k] = (float)std::cos(th);
+        P.csin[k] = (float)std::sin(th);
+    }
+    for (int i = 0; i < 9; ++i) P.R[i] = c->view_to_world[i];
+    if (na > 0)
+        for (int i = 0; i < 27; ++i) P.sh[i] = p->sh_rgb[i];
+    P.Y0 = (float)(0.5 * std::sqrt(1.0 / M_PI));
+    P.Y1 = (float)std::sqrt(3.0 / (4.0 * M_PI));
+    P.Y2 = (float)(0.5 * std::sqrt(15.0 / M_PI));
+    P.Y3 = (float)(0.25 * std::sqrt(5.0 / M_PI));
+    P.Y4 = (float)(0.25 * std::sqrt(15.0 / M_PI));
+}
+
+template <int NB, bool F16, bool INF_T>
+cudaError_t launch_tile(const ssilvb::GatherParams &P, cudaStream_t s) {
+    dim3 grid((P.W + 31) / 32, (P.H + 7) / 8);
+    ssilvb::gather_tile_kernel<NB, F16, INF_T><<<grid, 256, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch(const ssilvb::GatherParams &P, int nb, bool f16, bool inf_t, cudaStream_t s) {
+    if (nb == 32) {
+        if (f16) return inf_t ? launch_tile<32, true, true>(P, s) : launch_tile<32, true, false>(P, s);
+        return inf_t ? launch_tile<32, false, true>(P, s) : launch_tile<32, false, false>(P, s);
+    }
+    if (f16) return inf_t ? launch_tile<64, true, true>(P, s) : launch_tile<64, true, false>(P, s);
+    return inf_t ? launch_tile<64, false, true>(P, s) : launch_tile<64, false, false>(P, s);
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+int ssilvb_version(void) { return SSILVB_VERSION; }
+
+const char *ssilvb_status_string(ssilvb_status s) {
+    switch (s) {
+        case SSILVB_OK: return "SSILVB_OK";
+        case SSILVB_ERR_INVALID_ARG: return "SSILVB_ERR_INVALID_ARG";
+        case SSILVB_ERR_UNSUPPORTED: return "SSILVB_ERR_UNSUPPORTED";
+        case SSILVB_ERR_OUT_OF_MEMORY: return "SSILVB_ERR_OUT_OF_MEMORY";
+        case SSILVB_ERR_CUDA: return "SSILVB_ERR_CUDA";
+        case SSILVB_ERR_TIMEOUT: return "SSILVB_ERR_TIMEOUT";
+        case SSILVB_ERR_DEVICE_CHECK: return "SSILVB_ERR_DEVICE_CHECK";
+    }
+    return "SSILVB_UNKNOWN_STATUS";
+}
+
+const char *ssilvb_last_error(const ssilvb_ctx *ctx) { return ctx ? ctx->last_error.c_str() : g_create_error.c_str(); }
+
+ssilvb_status ssilvb_create(ssilvb_ctx **out_ctx, int cuda_device) {
+    if (!out_ctx) return fail(nullptr, SSILVB_ERR_INVALID_ARG, "out_ctx is NULL");
+    *out_ctx = nullptr;
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetDeviceCount");
+    if (cuda_device < 0 || cuda_device >= n)
+        return fail(nullptr, SSILVB_ERR_INVALID_ARG, "device %d outside 0..%d", cuda_device, n - 1);
+    ssilvb_ctx *ctx = new (std::nothrow) ssilvb_ctx();
+    if (!ctx) return fail(nullptr, SSILVB_ERR_OUT_OF_MEMORY, "host allocation failed");
+    ctx->device = cuda_device;
+    DeviceGuard dg(cuda_device);
+    e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, cuda_device);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        ssilvb_status s = cuda_fail(nullptr, e, "context set-up");
+        if (ctx->d_status) cudaFree(ctx->d_status);
+        delete ctx;
+        return e == cudaErrorMemoryAllocation ? SSILVB_ERR_OUT_OF_MEMORY : s;
+    }
+    *out_ctx = ctx;
+    return SSILVB_OK;
+}
+
+ssilvb_status ssilvb_destroy(ssilvb_ctx *ctx) {
+    if (!ctx) return SSILVB_OK;
+    DeviceGuard dg(ctx->device);
+    cudaDeviceSynchronize();
+    if (ctx->d_status) cudaFree(ctx->d_status);
+    if (ctx->stage) cudaFree(ctx->stage);
+    delete ctx;
+    return SSILVB_OK;
+}
+
+ssilvb_status ssilvb_gather(ssilvb_ctx *ctx, const ssilvb_gbuffer *gbuffer, const ssilvb_camera *camera,
+                            const ssilvb_params *params, const ssilvb_output *out, struct CUstream_st *stream) {
+    if (!ctx) return fail(nullptr, SSILVB_ERR_INVALID_ARG, "ctx is NULL");
+    ctx->last_error.clear();
+    DeviceGuard dg(ctx->device);
+    ssilvb_status s = validate(ctx, gbuffer, camera, params, out, true);
+    if (s != SSILVB_OK) return s;
+    ssilvb::GatherParams P;
+    fill_params(P, gbuffer, camera, params, out);
+    cudaError_t e = launch(P, params->sector_count, gbuffer->normal_fmt == SSILVB_FMT_F16X4,
+                           std::isinf(params->thickness), reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "gather launch");
+    return SSILVB_OK;
+}
+
+ssilvb_status ssilvb_gather_host(ssilvb_ctx *ctx, const ssilvb_gbuffer *gbuffer, const ssilvb_camera *camera,
+                                 const ssilvb_params *params, const ssilvb_output *out,
+                                 struct CUstream_st *stream) {
+    if (!ctx) return fail(nullptr, SSILVB_ERR_INVALID_ARG, "ctx is NULL");
+    ctx->last_error.clear();
+    DeviceGuard dg(ctx->device);
+    ssilvb_status s = validate(ctx, gbuffer, camera, params, out, false);
+    if (s != SSILVB_OK) return s;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const size_t W = gbuffer->width, H = gbuffer->height;
+    const size_t px = gbuffer->normal_fmt == SSILVB_FMT_F16X4 ? 8 : 16;
+    const int na = params->ambient_cones;
+    const size_t mask_bytes = out->masks ? (size_t)params->num_slices * W * H * (params->sector_count / 8) : 0;
+    auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
+    const size_t b_depth = up(W * H * 4), b_px = up(W * H * px), b_out = up(W * H * 16);
+    const size_t need = b_depth + 2 * b_px + b_out + (na > 0 ? b_out : 0) + up(mask_bytes);
+    if (need > ctx->stage_bytes) {
+        if (ctx->stage) {
+            cudaError_t e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "stream synchronize");
+            cudaFree(ctx->stage);
+            ctx->stage = nullptr;
+            ctx->stage_bytes = 0;
+        }
+        cudaError_t e = cudaMalloc(&ctx->stage, need);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, SSILVB_ERR_OUT_OF_MEMORY, "staging allocation of %zu bytes failed", need);
+        }
+        ctx->stage_bytes = need;
+    }
+    char *base = static_cast<char *>(ctx->stage);
+    float *d_depth = reinterpret_cast<float *>(base);
+    char *d_normal = base + b_depth;
+    char *d_rad = d_normal + b_px;
+    float *d_out0 = reinterpret_cast<float *>(d_rad + b_px);
+    float *d_out1 = na > 0 ? reinterpret_cast<float *>(reinterpret_cast<char *>(d_out0) + b_out) : nullptr;
+    void *d_masks = out->masks ? reinterpret_cast<char *>(d_out0) + b_out + (na > 0 ? b_out : 0) : nullptr;
+
+    cudaError_t e = cudaMemcpy2DAsync(d_depth, W * 4, gbuffer->depth, gbuffer->depth_pitch, W * 4, H,
+                                      cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(d_normal, W * px, gbuffer->normal, gbuffer->normal_pitch, W * px, H,
+                              cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(d_rad, W * px, gbuffer->radiance, gbuffer->radiance_pitch, W * px, H,
+                              cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "host-to-device copy");
+
+    ssilvb_gbuffer dg_ = *gbuffer;
+    dg_.depth = d_depth;
+    dg_.depth_pitch = W * 4;
+    dg_.normal = d_normal;
+    dg_.normal_pitch = W * px;
+    dg_.radiance = d_rad;
+    dg_.radiance_pitch = W * px;
+    ssilvb_output dout = {d_out0, W * 16, d_out1, W * 16, d_masks};
+    ssilvb::GatherParams P;
+    fill_params(P, &dg_, camera, params, &dout);
+    e = launch(P, params->sector_count, gbuffer->normal_fmt == SSILVB_FMT_F16X4, std::isinf(params->thickness), st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "gather launch");
+
+    e = cudaMemcpy2DAsync(out->out0, out->out0_pitch, d_out0, W * 16, W * 16, H, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && na > 0)
+        e = cudaMemcpy2DAsync(out->out1, out->out1_pitch, d_out1, W * 16, W * 16, H, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && out->masks)
+        e = cudaMemcpyAsync(out->masks, d_masks, mask_bytes, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "device-to-host copy");
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "gather execution");
+    return SSILVB_OK;
+}
+
+ssilvb_status ssilvb_synchronize(ssilvb_ctx *ctx, struct CUstream_st *stream) {
+    if (!ctx) return fail(nullptr, SSILVB_ERR_INVALID_ARG, "ctx is NULL");
+    DeviceGuard dg(ctx->device);
+    cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "stream execution");
+    int st = 0;
+    e = cudaMemcpy(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "status read");
+    if (st != 0) {
+        cudaMemset(ctx->d_status, 0, sizeof(int));
+        if (st == SSILVB_ERR_TIMEOUT) return fail(ctx, SSILVB_ERR_TIMEOUT, "a bounded device wait gave up");
+        return fail(ctx, SSILVB_ERR_DEVICE_CHECK, "device check failed (code %d)", st);
+    }
+    return SSILVB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,179 @@
+"""GPU parity: the CUDA gather (through the C ABI) against the CPU oracle.
+
+Bitmasks must equal the binary32 replica's bit for bit; AO, GI and ambient must be
+within 1e-4 of the FP64 oracle (Algorithm 1; Sections 3.1-3.3).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import scenegen
+from scenegen import Params
+from tests.gpu_util import check_parity, run_gpu, sample_pixels
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+
+    import paper_2301_11376_gb300 as ssilvb
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    ssilvb.build()
+    c = ssilvb.Context(0)
+    yield c
+    c.close()
+
+
+def test_256_full_frame(ctx):
+    w = scenegen.workload_256()
+    res = run_gpu(ctx, w.gbuf, w.params, w.noise)
+    info = check_parity(w.gbuf, w.params, w.noise, None, res)
+    assert info["agree"] > 0.999
+
+
+SMALL = [
+    # (W, H, seed, params kwargs, noise)
+    (1, 1, 3, dict(num_slices=2, steps_per_side=4), True),
+    (3, 5, 3, dict(num_slices=3, steps_per_side=5), True),
+    (37, 29, 4, dict(num_slices=16, steps_per_side=3, radius=4.0), True),
+    (61, 47, 5, dict(num_slices=1, steps_per_side=64, radius=3.0), True),
+    (50, 40, 6, dict(num_slices=4, steps_per_side=8, thickness=math.inf), True),
+    (50, 40, 7, dict(num_slices=4, steps_per_side=8, hit_rule=1), True),
+    (64, 48, 8, dict(num_slices=3, steps_per_side=8, sector_count=64, ambient_cones=8), True),
+    (64, 48, 9, dict(num_slices=2, steps_per_side=12, step_mode=1), True),
+    (64, 48, 10, dict(num_slices=2, steps_per_side=8, thickness=0.1, thickness_slope=0.05), True),
+    (64, 48, 11, dict(num_slices=2, steps_per_side=8, gi=False, ambient_cones=2), True),
+    (64, 48, 12, dict(num_slices=2, steps_per_side=8, ambient_cones=1), False),
+    (70, 33, 13, dict(num_slices=5, steps_per_side=7, sector_count=64, thickness=math.inf, hit_rule=1), True),
+    (33, 70, 14, dict(num_slices=4, steps_per_side=10, sector_count=64, step_mode=1, ambient_cones=4), True),
+]
+
+
+@pytest.mark.parametrize("W,H,seed,kw,use_noise", SMALL)
+def test_small_and_ragged(ctx, W, H, seed, kw, use_noise):
+    g = scenegen.render(seed, W, H, 8, 3)
+    prm = Params(**kw)
+    noise = scenegen.ign_table() if use_noise else None
+    sh = scenegen.sh_environment(7) if prm.ambient_cones else None
+    res = run_gpu(ctx, g, prm, noise, sh)
+    check_parity(g, prm, noise, sh, res, min_agree=0.95)
+
+
+@pytest.mark.parametrize("f16", [False, True])
+def test_fp16_storage(ctx, f16):
+    g = scenegen.render(15, 80, 60, 8, 3)
+    if f16:
+        g = g.as_f16()
+    prm = Params(num_slices=3, steps_per_side=10, ambient_cones=4)
+    noise, sh = scenegen.ign_table(), scenegen.sh_environment(7)
+    res = run_gpu(ctx, g, prm, noise, sh)
+    check_parity(g, prm, noise, sh, res)
+
+
+def test_pitched_inputs(ctx):
+    g = scenegen.render(16, 45, 31, 8, 3)
+    prm = Params(num_slices=2, steps_per_side=6)
+    noise = scenegen.ign_table()
+    a = run_gpu(ctx, g, prm, noise, pad=0)
+    b = run_gpu(ctx, g, prm, noise, pad=11)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[2], b[2])
+    check_parity(g, prm, noise, None, b)
+
+
+def test_sky_only_frame(ctx):
+    g = scenegen.render(17, 40, 30, 0, 0)
+    g.depth[:] = np.inf
+    prm = Params(num_slices=2, steps_per_side=4, ambient_cones=4)
+    sh = scenegen.sh_environment(7)
+    o0, o1, m = run_gpu(ctx, g, prm, None, sh)
+    assert np.all(o0 == [0, 0, 0, 1]) and np.all(o1 == 0) and np.all(m == 0)
+
+
+def test_flat_plane_exact(ctx):
+    g = scenegen.hand_plane(41, 33, normal_view=(0.5, -0.3, 0.81), point_depth=6.0)
+    prm = Params(num_slices=4, steps_per_side=7, radius=2.0, thickness=0.5)
+    o0, _, m = run_gpu(ctx, g, prm, None)
+    assert np.all(m == 0) and np.all(o0[:, 3] == 1.0) and np.all(o0[:, :3] == 0.0)
+
+
+def test_deterministic_and_stream(ctx):
+    import torch
+    g = scenegen.render(18, 64, 64, 8, 3)
+    prm = Params(num_slices=4, steps_per_side=8)
+    noise = scenegen.ign_table()
+    s = torch.cuda.Stream()
+    a = run_gpu(ctx, g, prm, noise, stream=s)
+    b = run_gpu(ctx, g, prm, noise)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[2], b[2])
+
+
+def test_1080p_full_masks_and_sampled_fp64(ctx):
+    w = scenegen.workload_1080p()
+    res = run_gpu(ctx, w.gbuf, w.params, w.noise)
+    H, W = w.gbuf.depth.shape
+    # masks of every pixel against the replica
+    prob = oracle.Problem(w.gbuf, w.params, w.noise)
+    _, _, rm = oracle.fp32(prob)
+    assert np.array_equal(res[2], rm)
+    check_parity(w.gbuf, w.params, w.noise, None, res, pixels=sample_pixels(H, W, 20000, 1))
+
+
+@pytest.mark.parametrize("nb", [32, 64])
+def test_4k_precision_form_sampled(ctx, nb):
+    """The benchmark workload at full size and launch configuration, checked on sampled pixels:
+    FP32 depth with FP16 normal/radiance, 4 slices, 32 steps, 4 ambient cones."""
+    w = scenegen.workload_4k(sector_count=nb)
+    res = run_gpu(ctx, w.gbuf, w.params, w.noise, w.sh)
+    H, W = w.gbuf.depth.shape
+    info = check_parity(w.gbuf, w.params, w.noise, w.sh, res, pixels=sample_pixels(H, W, 12000, 2))
+    assert info["agree"] > 0.98
+
+
+def test_host_buffers_equal_device_buffers(ctx):
+    import torch
+
+    import paper_2301_11376_gb300 as ssilvb
+    g = scenegen.render(19, 72, 40, 8, 3).as_f16()
+    prm = Params(num_slices=2, steps_per_side=8, ambient_cones=4)
+    noise, sh = scenegen.ign_table(), scenegen.sh_environment(7)
+    a = run_gpu(ctx, g, prm, noise, sh)
+    H, W = g.depth.shape
+    o0 = np.zeros((H, W, 4), np.float32)
+    o1 = np.zeros((H, W, 4), np.float32)
+    m = np.zeros((prm.num_slices, H, W), np.uint32)
+    ctx.gather_host(g.depth, g.normal, g.radiance, g.camera, prm, o0, o1, m, noise=noise, sh=sh)
+    assert np.array_equal(o0.reshape(-1, 4), a[0].astype(np.float32))
+    assert np.array_equal(o1.reshape(-1, 4), a[1].astype(np.float32))
+    assert np.array_equal(m.reshape(prm.num_slices, -1).T.astype(np.uint64), a[2])
+    del torch, ssilvb
+
+
+def test_invalid_arguments_enqueue_nothing(ctx):
+    import torch
+
+    import paper_2301_11376_gb300 as ssilvb
+    g = scenegen.render(20, 32, 32, 4, 1)
+    d = torch.from_numpy(g.depth).cuda()
+    n = torch.from_numpy(g.normal).cuda()
+    r = torch.from_numpy(g.radiance).cuda()
+    out0 = torch.full((32, 32, 4), 5.0, device="cuda")
+    bad = [Params(num_slices=0), Params(num_slices=17), Params(steps_per_side=65), Params(radius=-1.0),
+           Params(thickness=0.0), Params(sector_count=48), Params(hit_rule=2), Params(ambient_cones=3)]
+    for prm in bad:
+        with pytest.raises(ssilvb.SsilvbError) as ei:
+            ctx.gather(d, n, r, g.camera, prm, out0, None, None)
+        assert ei.value.code == 1
+    with pytest.raises(ssilvb.SsilvbError) as ei:
+        ctx.gather(d, n, r, g.camera, Params(sector_count=128), out0, None, None)
+    assert ei.value.code == 2
+    with pytest.raises(ssilvb.SsilvbError):
+        ctx.gather(d, n.half(), r, g.camera, Params(), out0, None, None)
+    # a host pointer where device memory is required
+    with pytest.raises(ssilvb.SsilvbError):
+        ctx.gather(torch.from_numpy(g.depth), n, r, g.camera, Params(), out0, None, None)
+    torch.cuda.synchronize()
+    assert torch.all(out0 == 5.0)
