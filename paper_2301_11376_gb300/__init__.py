@@ -224,7 +224,9 @@ class Context:
         pc = _params_c(params, keep, noise, sh)
         o = Output(out0.data_ptr(), _pitch(out0, 4), out1.data_ptr() if out1 is not None else None,
                    _pitch(out1, 4) if out1 is not None else 0, masks.data_ptr() if masks is not None else None)
-        s = stream if stream is not None else torch.cuda.current_stream(depth.device)
+        if stream is None:
+            stream = torch.cuda.current_stream(depth.device if depth.is_cuda else None)
+        s = stream
         self._check(self.lib.ssilvb_gather(self.handle, ctypes.byref(g), ctypes.byref(_camera_c(camera)),
                                            ctypes.byref(pc), ctypes.byref(o), ctypes.c_void_p(s.cuda_stream)))
 
