@@ -118,6 +118,18 @@ typedef struct {
     void *masks;
 } ssilvb_output;
 
+/* Launch choices that do not change any result (every choice gives bit-identical output). */
+typedef enum {
+    SSILVB_MAP_AUTO = 0,  /* library default */
+    SSILVB_MAP_TILE = 1,  /* one thread per pixel, 32 x 8 pixel tiles */
+    SSILVB_MAP_CLASS = 2  /* one thread per pixel; the 32 lanes of a warp share a 4x4 noise class */
+} ssilvb_mapping;
+
+typedef struct {
+    int mapping;          /* ssilvb_mapping */
+    int reserved[7];      /* must be zero */
+} ssilvb_tuning;
+
 /* Library version, major * 10000 + minor * 100 + patch. */
 int ssilvb_version(void);
 
@@ -151,6 +163,9 @@ ssilvb_status ssilvb_gather(ssilvb_ctx *ctx, const ssilvb_gbuffer *gbuffer, cons
 ssilvb_status ssilvb_gather_host(ssilvb_ctx *ctx, const ssilvb_gbuffer *gbuffer, const ssilvb_camera *camera,
                                  const ssilvb_params *params, const ssilvb_output *out,
                                  struct CUstream_st *stream);
+
+/* Set the context's launch choices for later calls (copied).  INVALID_ARG on an unknown value. */
+ssilvb_status ssilvb_set_tuning(ssilvb_ctx *ctx, const ssilvb_tuning *tuning);
 
 /* Wait for the work enqueued on stream and report a failure of it: CUDA
  * (asynchronous launch or execution error) or DEVICE_CHECK / TIMEOUT from the

@@ -123,6 +123,8 @@ int orc32_pixels(const orc_problem *pb, int n, const int32_t *xy, float *out0, f
     const float half_nb = 0.5f * (float)nb, f_nb = (float)nb;
     const float inv_nb = 1.0f / (float)nb, inv_nd = 1.0f / (float)nd;
     const float t0 = pb->thickness, kt = pb->thickness_slope;
+    const float edge_hi = pb->hit_rule == 0 ? f_nb - 0.5f : nextafterf(f_nb, 0.0f);
+    const float edge_lo = pb->hit_rule == 0 ? 0.5f : nextafterf(0.0f, 1.0f);
 
     /* Direction table: cos, sin of (i + xi_phi) pi / N_d per noise class, FP64 rounded once. */
     float dcos[16][16], dsin[16][16];
@@ -240,7 +242,12 @@ int orc32_pixels(const orc_problem *pb, int n, const int32_t *xy, float *out0, f
                     const float rl = orc32_rsqrt(ll);
                     const float cf = clamp1(dv * rl);
                     const float Xf = fminf(fmaxf(fmaf(orc32_acos(cf), sK, off), 0.0f), f_nb);
-                    ops += 2 + 2 + 3 + 6 + RSQRT_OPS + 3 + ACOS_OPS + 3;
+                    ops += 2 + 2 + 3 + 6 + RSQRT_OPS + 3 + ACOS_OPS + 3 + 1;
+                    /* The back endpoint is at or beyond the front one toward this side's edge, so a
+                     * front endpoint inside the edge band occludes no sector (Section 3.1 hit rule):
+                     * the band is half a sector for the half-covered rule, the edge itself for the
+                     * floor/ceil rule.  The sample ends here. */
+                    if (pos ? Xf > edge_hi : Xf < edge_lo) continue;
 
                     /* Back sample (constant thickness behind the front one). */
                     float Xb;

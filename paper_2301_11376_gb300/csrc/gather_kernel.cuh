@@ -51,6 +51,7 @@ struct GatherParams {
     // per-launch binary32 constants
     float inv_fx, inv_fy, kx0, ninv_fy, ky0;
     float Rfx, dn, K, half_nb, f_nb, inv_nb, inv_nd;
+    float edge_hi, edge_lo;  // front endpoints beyond these occlude nothing (side +omega / -omega)
     float t0, kt;
     float xi_s[16];
     float dcos[16][kMaxSlices];
@@ -152,13 +153,96 @@ __device__ __forceinline__ float3 load_xyz(const char *base, size_t pitch, int x
     }
 }
 
-__device__ __forceinline__ bool is_geometry(float z) { return z > 0.0f && z < __int_as_float(0x7f800000); }
+// 0 < z < +INF (NaN and negative values fail): positive finite binary32 bit patterns are 1 .. 0x7f7fffff.
+__device__ __forceinline__ bool is_geometry(float z) { return __float_as_uint(z) - 1u < 0x7f7fffffu; }
 
-// The whole per-pixel gather.  cls is the pixel's 4x4 noise class (y & 3) * 4 + (x & 3).
+// Which pixel step j of a side reads (nearest pixel, ties to even, through the 1.5*2^23
+// add), whether it is on screen and not the centre pixel, and its depth (loaded now so
+// that the load overlaps the previous sample's arithmetic).
+struct Step {
+    float dxf, dyf;  // integer pixel offsets as floats
+    int qx, qy;
+    float zq;        // depth at the sample pixel (0 when the step is off-screen or the centre)
+    bool on;         // the sample pixel is on screen
+    bool ok;         // on screen and not the centre pixel
+};
+
+template <int STEP_MODE>
+__device__ __forceinline__ Step make_step(const GatherParams &P, int x, int y, float jf, float xidn, float rpx,
+                                          float wsx, float wsy) {
+    Step s;
+    const float uj = fmaf(jf, P.dn, xidn);
+    const float o = STEP_MODE == 0 ? uj * rpx : (uj * uj) * rpx;
+    const float rx = o * wsx + kMagic, ry = o * wsy + kMagic;
+    const int dx = __float_as_int(rx) - kMagicBits, dy = __float_as_int(ry) - kMagicBits;
+    s.dxf = rx - kMagic;
+    s.dyf = ry - kMagic;
+    s.qx = x + dx;
+    s.qy = y + dy;
+    s.on = (unsigned)s.qx < (unsigned)P.W && (unsigned)s.qy < (unsigned)P.H;
+    s.ok = s.on && ((dx | dy) != 0);
+    s.zq = 0.0f;
+    if (s.ok) s.zq = __ldg(P.depth + (unsigned)s.qy * (unsigned)P.depth_pitch + (unsigned)s.qx);
+    return s;
+}
+
+// Per-pixel state the sample loop reads.
+struct Pixel {
+    float z, u, v, px, py, vx, vy, vz, tp, t2, m2t;
+    float3 n;
+};
+
 template <int NB, bool F16, bool INF_T>
+__device__ __forceinline__ void process_step(const GatherParams &P, const Pixel &X, const Step &s, float sK,
+                                             float edge, float off, typename MaskT<NB>::T &b, float &GIr,
+                                             float &GIg, float &GIb) {
+    using M = typename MaskT<NB>::T;
+    const float zq = s.zq;
+    // Front sample s_f, l = s_f - p, its cosine to v and its sector coordinate.
+    const float uq = X.u + s.dxf, vq = X.v + s.dyf;
+    const float aq = fmaf(uq, P.inv_fx, P.kx0), bq = fmaf(vq, P.ninv_fy, P.ky0);
+    const float lx = fmaf(aq, zq, -X.px), ly = fmaf(bq, zq, -X.py), lz = X.z - zq;
+    const float dv = fmaf(lx, X.vx, fmaf(ly, X.vy, lz * X.vz));
+    const float ll = fmaf(lx, lx, fmaf(ly, ly, lz * lz));
+    const float rl = own_rsqrt(ll);
+    const float Xf = fminf(fmaxf(fmaf(own_acos(clamp1(dv * rl)), sK, off), 0.0f), P.f_nb);
+    // The back endpoint lies at or beyond the front one toward this side's hemisphere edge, so
+    // a front endpoint within the edge band (half a sector for the half-covered rule, the edge
+    // itself for the floor/ceil rule) cannot occlude any sector: nothing more to do.
+    if (sK > 0.0f ? Xf > P.edge_hi : Xf < P.edge_lo) return;
+    // Back sample, thickness t behind the front one along the centre pixel's view ray.
+    float Xb;
+    if (INF_T) {
+        Xb = edge;
+    } else {
+        const float dvb = dv - X.tp;
+        const float llb = fmaf(X.m2t, dv, ll + X.t2);
+        const float cb = clamp1(dvb * own_rsqrt(llb));
+        Xb = fminf(fmaxf(fmaf(own_acos(cb), sK, off), 0.0f), P.f_nb);
+    }
+    const float A = fminf(Xf, Xb), B = fmaxf(Xf, Xb);
+    const M bj = sector_run<NB>(A, B, P.hit_rule);
+    const int newly = popc_(bj & ~b);
+    b |= bj;
+    // Indirect light of the newly occluded sectors (Section 3.3).
+    if (newly > 0 && P.gi) {
+        const float3 cj = load_xyz<F16>(P.radiance, P.radiance_pitch, s.qx, s.qy);
+        const float3 nj = load_xyz<F16>(P.normal, P.normal_pitch, s.qx, s.qy);
+        const float cp = fmaxf(fmaf(X.n.x, lx, fmaf(X.n.y, ly, X.n.z * lz)) * rl, 0.0f);
+        const float cq = fmaxf(-(fmaf(nj.x, lx, fmaf(nj.y, ly, nj.z * lz)) * rl), 0.0f);
+        const float wgt = (((float)newly * P.inv_nb) * cp) * cq;
+        GIr = fmaf(wgt, cj.x, GIr);
+        GIg = fmaf(wgt, cj.y, GIg);
+        GIb = fmaf(wgt, cj.z, GIb);
+    }
+}
+
+// The whole per-pixel gather (Algorithm 1 with Sections 3.2 and 3.3) for pixel (x, y) of
+// noise class cls = (y & 3) * 4 + (x & 3).
+template <int NB, bool F16, bool INF_T, int STEP_MODE>
 __device__ __forceinline__ void gather_pixel(const GatherParams &P, int x, int y) {
     using M = typename MaskT<NB>::T;
-    const float z = __ldg(P.depth + (size_t)y * P.depth_pitch + x);
+    const float z = __ldg(P.depth + (unsigned)y * (unsigned)P.depth_pitch + (unsigned)x);
     float4 *o0 = reinterpret_cast<float4 *>(P.out0 + (size_t)y * P.out0_pitch) + x;
     if (!is_geometry(z)) {
         *o0 = make_float4(0.0f, 0.0f, 0.0f, 1.0f);
@@ -169,20 +253,26 @@ __device__ __forceinline__ void gather_pixel(const GatherParams &P, int x, int y
     }
 
     // Pixel setup (Algorithm 1: p, n_p, projected radius, step size).
-    const float u = (float)x + 0.5f, v = (float)y + 0.5f;
-    const float ax = fmaf(u, P.inv_fx, P.kx0), by = fmaf(v, P.ninv_fy, P.ky0);
-    const float px = ax * z, py = by * z;
+    Pixel X;
+    X.z = z;
+    X.u = (float)x + 0.5f;
+    X.v = (float)y + 0.5f;
+    const float ax = fmaf(X.u, P.inv_fx, P.kx0), by = fmaf(X.v, P.ninv_fy, P.ky0);
+    X.px = ax * z;
+    X.py = by * z;
     const float rd = own_rsqrt(fmaf(ax, ax, fmaf(by, by, 1.0f)));
-    const float vx = -(ax * rd), vy = -(by * rd), vz = rd;
-    const float3 n = load_xyz<F16>(P.normal, P.normal_pitch, x, y);
+    X.vx = -(ax * rd);
+    X.vy = -(by * rd);
+    X.vz = rd;
+    X.n = load_xyz<F16>(P.normal, P.normal_pitch, x, y);
     const float rpx = fminf(P.Rfx / z, 1048576.0f);
     const int cls = (y & 3) * 4 + (x & 3);
     const float xidn = P.xi_s[cls] * P.dn;
-    float tp = 0.0f, t2 = 0.0f, m2t = 0.0f;
+    X.tp = X.t2 = X.m2t = 0.0f;
     if (!INF_T) {
-        tp = fmaf(P.kt, z, P.t0);
-        t2 = tp * tp;
-        m2t = -2.0f * tp;
+        X.tp = fmaf(P.kt, z, P.t0);
+        X.t2 = X.tp * X.tp;
+        X.m2t = -2.0f * X.tp;
     }
 
     float AO = 0.0f, GIr = 0.0f, GIg = 0.0f, GIb = 0.0f, AMr = 0.0f, AMg = 0.0f, AMb = 0.0f;
@@ -190,13 +280,13 @@ __device__ __forceinline__ void gather_pixel(const GatherParams &P, int x, int y
         const float cphi = P.dcos[cls][i], sphi = P.dsin[cls][i];
         // Slice plane: s = normalize(w3 - (w3.v) v), w3 the view-space image of omega.
         const float w3x = cphi * P.inv_fx, w3y = -(sphi * P.inv_fy);
-        const float wv = fmaf(w3x, vx, w3y * vy);
-        const float sx0 = fmaf(-wv, vx, w3x), sy0 = fmaf(-wv, vy, w3y), sz0 = -(wv * vz);
+        const float wv = fmaf(w3x, X.vx, w3y * X.vy);
+        const float sx0 = fmaf(-wv, X.vx, w3x), sy0 = fmaf(-wv, X.vy, w3y), sz0 = -(wv * X.vz);
         const float rs = own_rsqrt(fmaf(sx0, sx0, fmaf(sy0, sy0, sz0 * sz0)));
         const float sx = sx0 * rs, sy = sy0 * rs, sz = sz0 * rs;
-        // Projected normal angle gamma (sector frame centred on it, Eq. 4).
-        const float nv = fmaf(n.x, vx, fmaf(n.y, vy, n.z * vz));
-        const float nsd = fmaf(n.x, sx, fmaf(n.y, sy, n.z * sz));
+        // Projected normal angle gamma (the sector frame is centred on it, Eq. 4).
+        const float nv = fmaf(X.n.x, X.vx, fmaf(X.n.y, X.vy, X.n.z * X.vz));
+        const float nsd = fmaf(X.n.x, sx, fmaf(X.n.y, sy, X.n.z * sz));
         const float pn2 = fmaf(nv, nv, nsd * nsd);
         float cg = 1.0f, sg = 0.0f, gam = 0.0f;
         if (pn2 > 0.0f) {
@@ -209,58 +299,18 @@ __device__ __forceinline__ void gather_pixel(const GatherParams &P, int x, int y
         const float off = fmaf(-gam, P.K, P.half_nb);
 
         M b = 0;
-#pragma unroll
+        // Side -omega, then side +omega, near to far.  Once a step leaves the screen every later
+        // step of that side does too (the rounded offset is monotone in j), so the side ends there.
+#pragma unroll 1
         for (int side = 0; side < 2; ++side) {
-            const bool pos = side == 1;
-            const float wsx = pos ? cphi : -cphi, wsy = pos ? sphi : -sphi;
-            const float sK = pos ? P.K : -P.K;
-            const float edge = pos ? P.f_nb : 0.0f;
+            const float sgn = side ? 1.0f : -1.0f;
+            const float wsx = sgn * cphi, wsy = sgn * sphi, sK = sgn * P.K;
+            const float edge = side ? P.f_nb : 0.0f;
 #pragma unroll 2
             for (int j = 0; j < P.ns; ++j) {
-                const float uj = fmaf((float)(j + 1), P.dn, xidn);
-                const float o = P.step_mode == 0 ? uj * rpx : (uj * uj) * rpx;
-                const float rx = o * wsx + kMagic, ry = o * wsy + kMagic;
-                const int dx = __float_as_int(rx) - kMagicBits, dy = __float_as_int(ry) - kMagicBits;
-                if ((dx | dy) == 0) continue;
-                const int qx = x + dx, qy = y + dy;
-                if ((unsigned)qx >= (unsigned)P.W || (unsigned)qy >= (unsigned)P.H) continue;
-                const float zq = __ldg(P.depth + (size_t)qy * P.depth_pitch + qx);
-                if (!is_geometry(zq)) continue;
-
-                // Front sample.
-                const float uq = u + (rx - kMagic), vq = v + (ry - kMagic);
-                const float aq = fmaf(uq, P.inv_fx, P.kx0), bq = fmaf(vq, P.ninv_fy, P.ky0);
-                const float lx = fmaf(aq, zq, -px), ly = fmaf(bq, zq, -py), lz = z - zq;
-                const float dv = fmaf(lx, vx, fmaf(ly, vy, lz * vz));
-                const float ll = fmaf(lx, lx, fmaf(ly, ly, lz * lz));
-                const float rl = own_rsqrt(ll);
-                const float Xf = fminf(fmaxf(fmaf(own_acos(clamp1(dv * rl)), sK, off), 0.0f), P.f_nb);
-                // Back sample, thickness t behind the front one.
-                float Xb;
-                if (INF_T) {
-                    Xb = edge;
-                } else {
-                    const float dvb = dv - tp;
-                    const float llb = fmaf(m2t, dv, ll + t2);
-                    const float cb = clamp1(dvb * own_rsqrt(llb));
-                    Xb = fminf(fmaxf(fmaf(own_acos(cb), sK, off), 0.0f), P.f_nb);
-                }
-                const float A = fminf(Xf, Xb), B = fmaxf(Xf, Xb);
-                const M bj = sector_run<NB>(A, B, P.hit_rule);
-                const int newly = popc_(bj & ~b);
-                b |= bj;
-
-                // Indirect light of the newly occluded sectors (Section 3.3).
-                if (newly > 0 && P.gi) {
-                    const float3 cj = load_xyz<F16>(P.radiance, P.radiance_pitch, qx, qy);
-                    const float3 nj = load_xyz<F16>(P.normal, P.normal_pitch, qx, qy);
-                    const float cp = fmaxf(fmaf(n.x, lx, fmaf(n.y, ly, n.z * lz)) * rl, 0.0f);
-                    const float cq = fmaxf(-(fmaf(nj.x, lx, fmaf(nj.y, ly, nj.z * lz)) * rl), 0.0f);
-                    const float wgt = (((float)newly * P.inv_nb) * cp) * cq;
-                    GIr = fmaf(wgt, cj.x, GIr);
-                    GIg = fmaf(wgt, cj.y, GIg);
-                    GIb = fmaf(wgt, cj.z, GIb);
-                }
+                const Step st = make_step<STEP_MODE>(P, x, y, (float)(j + 1), xidn, rpx, wsx, wsy);
+                if (!st.on) break;
+                if (st.ok && is_geometry(st.zq)) process_step<NB, F16, INF_T>(P, X, st, sK, edge, off, b, GIr, GIg, GIb);
             }
         }
 
@@ -273,7 +323,7 @@ __device__ __forceinline__ void gather_pixel(const GatherParams &P, int x, int y
                 const int freek = popc_(~b & Mk);
                 const float ck = fmaf(cg, P.ccos[k], -(sg * P.csin[k]));
                 const float sk = fmaf(sg, P.ccos[k], cg * P.csin[k]);
-                const float a3x = fmaf(ck, vx, sk * sx), a3y = fmaf(ck, vy, sk * sy), a3z = fmaf(ck, vz, sk * sz);
+                const float a3x = fmaf(ck, X.vx, sk * sx), a3y = fmaf(ck, X.vy, sk * sy), a3z = fmaf(ck, X.vz, sk * sz);
                 const float wx = fmaf(P.R[0], a3x, fmaf(P.R[1], a3y, P.R[2] * a3z));
                 const float wy = fmaf(P.R[3], a3x, fmaf(P.R[4], a3y, P.R[5] * a3z));
                 const float wz = fmaf(P.R[6], a3x, fmaf(P.R[7], a3y, P.R[8] * a3z));
@@ -308,13 +358,29 @@ __device__ __forceinline__ void gather_pixel(const GatherParams &P, int x, int y
             make_float4(AMr * P.inv_nd, AMg * P.inv_nd, AMb * P.inv_nd, 0.0f);
 }
 
-// One thread per pixel, 32 x 8 pixel tiles.
-template <int NB, bool F16, bool INF_T>
+// Natural mapping: one thread per pixel, 32 x 8 pixel tiles.
+template <int NB, bool F16, bool INF_T, int STEP_MODE>
 __global__ void __launch_bounds__(256) gather_tile_kernel(const __grid_constant__ GatherParams P) {
     const int x = blockIdx.x * 32 + (threadIdx.x & 31);
     const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
     if (x >= P.W || y >= P.H) return;
-    gather_pixel<NB, F16, INF_T>(P, x, y);
+    gather_pixel<NB, F16, INF_T, STEP_MODE>(P, x, y);
+}
+
+// Class-strided mapping: a block covers 128 consecutive pixels of one row; warp w takes the
+// pixels with x = 4 * lane + w, so all 32 lanes share a 4x4 noise class and therefore the
+// slice directions and step offsets: their samples land on neighbouring pixels and the
+// depth gathers of a warp touch a few cache lines instead of one per lane.
+#ifndef SSILVB_CLASS_MIN_BLOCKS
+#define SSILVB_CLASS_MIN_BLOCKS 5
+#endif
+template <int NB, bool F16, bool INF_T, int STEP_MODE>
+__global__ void __launch_bounds__(128, SSILVB_CLASS_MIN_BLOCKS) gather_class_kernel(const __grid_constant__ GatherParams P) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int x = blockIdx.x * 128 + 4 * lane + w;
+    const int y = blockIdx.y;
+    if (x >= P.W) return;
+    gather_pixel<NB, F16, INF_T, STEP_MODE>(P, x, y);
 }
 
 }  // namespace ssilvb

@@ -24,6 +24,7 @@ struct ssilvb_ctx {
     // staging for ssilvb_gather_host
     void *stage = nullptr;
     size_t stage_bytes = 0;
+    ssilvb_tuning tuning = {SSILVB_MAP_AUTO, {0, 0, 0, 0, 0, 0, 0}};
 };
 
 namespace {
@@ -63,6 +64,8 @@ ssilvb_status validate(ssilvb_ctx *ctx, const ssilvb_gbuffer *g, const ssilvb_ca
     const size_t W = (size_t)g->width;
     if (g->depth_pitch < W * 4 || g->depth_pitch % 4)
         return fail(ctx, SSILVB_ERR_INVALID_ARG, "depth pitch %zu invalid for width %zu", g->depth_pitch, W);
+    if ((g->depth_pitch / 4) * (size_t)g->height >= ((size_t)1 << 31))
+        return fail(ctx, SSILVB_ERR_INVALID_ARG, "depth plane larger than 2^31 elements");
     if (g->normal_pitch < W * px || g->normal_pitch % px || g->radiance_pitch < W * px || g->radiance_pitch % px)
         return fail(ctx, SSILVB_ERR_INVALID_ARG, "normal/radiance pitch invalid (pixel size %zu)", px);
     if (!aligned(g->depth, 16) || !aligned(g->normal, 16) || !aligned(g->radiance, 16))
@@ -78,7 +81,8 @@ ssilvb_status validate(ssilvb_ctx *ctx, const ssilvb_gbuffer *g, const ssilvb_ca
         return fail(ctx, SSILVB_ERR_INVALID_ARG, "steps_per_side %d outside 1..64", p->steps_per_side);
     if (!(p->radius > 0.0f) || !std::isfinite(p->radius))
         return fail(ctx, SSILVB_ERR_INVALID_ARG, "radius must be finite and > 0");
-    if (!(p->thickness > 0.0f)) return fail(ctx, SSILVB_ERR_INVALID_ARG, "thickness must be > 0 (+INF allowed)");
+    if (!(p->thickness > 0.0f) || (std::isfinite(p->thickness) && p->thickness > 1e6f))
+        return fail(ctx, SSILVB_ERR_INVALID_ARG, "thickness must be in (0, 1e6] or +INF");
     if (!(p->thickness_slope >= 0.0f) || !std::isfinite(p->thickness_slope))
         return fail(ctx, SSILVB_ERR_INVALID_ARG, "thickness_slope must be finite and >= 0");
     if (p->sector_count == 128) return fail(ctx, SSILVB_ERR_UNSUPPORTED, "sector_count 128 is not built");
@@ -161,6 +165,8 @@ void fill_params(ssilvb::GatherParams &P, const ssilvb_gbuffer *g, const ssilvb_
     P.f_nb = (float)nb;
     P.inv_nb = 1.0f / (float)nb;
     P.inv_nd = 1.0f / (float)nd;
+    P.edge_hi = p->hit_rule == 0 ? P.f_nb - 0.5f : std::nextafter(P.f_nb, 0.0f);
+    P.edge_lo = p->hit_rule == 0 ? 0.5f : std::nextafter(0.0f, 1.0f);
     P.t0 = p->thickness;
     P.kt = p->thickness_slope;
     for (int cl = 0; cl < 16; ++cl) {
@@ -187,20 +193,32 @@ void fill_params(ssilvb::GatherParams &P, const ssilvb_gbuffer *g, const ssilvb_
     P.Y4 = (float)(0.25 * std::sqrt(15.0 / M_PI));
 }
 
-template <int NB, bool F16, bool INF_T>
-cudaError_t launch_tile(const ssilvb::GatherParams &P, cudaStream_t s) {
-    dim3 grid((P.W + 31) / 32, (P.H + 7) / 8);
-    ssilvb::gather_tile_kernel<NB, F16, INF_T><<<grid, 256, 0, s>>>(P);
+template <int NB, bool F16, bool INF_T, int SM>
+cudaError_t launch_t(const ssilvb::GatherParams &P, int mapping, cudaStream_t s) {
+    if (mapping == SSILVB_MAP_TILE) {
+        dim3 grid((P.W + 31) / 32, (P.H + 7) / 8);
+        ssilvb::gather_tile_kernel<NB, F16, INF_T, SM><<<grid, 256, 0, s>>>(P);
+    } else {
+        dim3 grid((P.W + 127) / 128, P.H);
+        ssilvb::gather_class_kernel<NB, F16, INF_T, SM><<<grid, 128, 0, s>>>(P);
+    }
     return cudaGetLastError();
 }
 
-cudaError_t launch(const ssilvb::GatherParams &P, int nb, bool f16, bool inf_t, cudaStream_t s) {
-    if (nb == 32) {
-        if (f16) return inf_t ? launch_tile<32, true, true>(P, s) : launch_tile<32, true, false>(P, s);
-        return inf_t ? launch_tile<32, false, true>(P, s) : launch_tile<32, false, false>(P, s);
-    }
-    if (f16) return inf_t ? launch_tile<64, true, true>(P, s) : launch_tile<64, true, false>(P, s);
-    return inf_t ? launch_tile<64, false, true>(P, s) : launch_tile<64, false, false>(P, s);
+template <int NB, bool F16, bool INF_T>
+cudaError_t launch_s(const ssilvb::GatherParams &P, int mapping, cudaStream_t s) {
+    return P.step_mode == 0 ? launch_t<NB, F16, INF_T, 0>(P, mapping, s) : launch_t<NB, F16, INF_T, 1>(P, mapping, s);
+}
+
+template <int NB>
+cudaError_t launch_nb(const ssilvb::GatherParams &P, bool f16, bool inf_t, int mapping, cudaStream_t s) {
+    if (f16) return inf_t ? launch_s<NB, true, true>(P, mapping, s) : launch_s<NB, true, false>(P, mapping, s);
+    return inf_t ? launch_s<NB, false, true>(P, mapping, s) : launch_s<NB, false, false>(P, mapping, s);
+}
+
+cudaError_t launch(const ssilvb::GatherParams &P, int nb, bool f16, bool inf_t, int mapping, cudaStream_t s) {
+    if (mapping == SSILVB_MAP_AUTO) mapping = SSILVB_MAP_CLASS;
+    return nb == 32 ? launch_nb<32>(P, f16, inf_t, mapping, s) : launch_nb<64>(P, f16, inf_t, mapping, s);
 }
 
 struct DeviceGuard {
@@ -281,7 +299,7 @@ ssilvb_status ssilvb_gather(ssilvb_ctx *ctx, const ssilvb_gbuffer *gbuffer, cons
     ssilvb::GatherParams P;
     fill_params(P, gbuffer, camera, params, out);
     cudaError_t e = launch(P, params->sector_count, gbuffer->normal_fmt == SSILVB_FMT_F16X4,
-                           std::isinf(params->thickness), reinterpret_cast<cudaStream_t>(stream));
+                           std::isinf(params->thickness), ctx->tuning.mapping, reinterpret_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "gather launch");
     return SSILVB_OK;
 }
@@ -345,7 +363,8 @@ ssilvb_status ssilvb_gather_host(ssilvb_ctx *ctx, const ssilvb_gbuffer *gbuffer,
     ssilvb_output dout = {d_out0, W * 16, d_out1, W * 16, d_masks};
     ssilvb::GatherParams P;
     fill_params(P, &dg_, camera, params, &dout);
-    e = launch(P, params->sector_count, gbuffer->normal_fmt == SSILVB_FMT_F16X4, std::isinf(params->thickness), st);
+    e = launch(P, params->sector_count, gbuffer->normal_fmt == SSILVB_FMT_F16X4, std::isinf(params->thickness),
+               ctx->tuning.mapping, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "gather launch");
 
     e = cudaMemcpy2DAsync(out->out0, out->out0_pitch, d_out0, W * 16, W * 16, H, cudaMemcpyDeviceToHost, st);
@@ -356,6 +375,15 @@ ssilvb_status ssilvb_gather_host(ssilvb_ctx *ctx, const ssilvb_gbuffer *gbuffer,
     if (e != cudaSuccess) return cuda_fail(ctx, e, "device-to-host copy");
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "gather execution");
+    return SSILVB_OK;
+}
+
+ssilvb_status ssilvb_set_tuning(ssilvb_ctx *ctx, const ssilvb_tuning *tuning) {
+    if (!ctx) return fail(nullptr, SSILVB_ERR_INVALID_ARG, "ctx is NULL");
+    if (!tuning) return fail(ctx, SSILVB_ERR_INVALID_ARG, "tuning is NULL");
+    if (tuning->mapping < SSILVB_MAP_AUTO || tuning->mapping > SSILVB_MAP_CLASS)
+        return fail(ctx, SSILVB_ERR_INVALID_ARG, "unknown mapping %d", tuning->mapping);
+    ctx->tuning = *tuning;
     return SSILVB_OK;
 }
 
