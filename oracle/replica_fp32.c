@@ -33,7 +33,7 @@
 #include "oracle.h"
 
 #define RSQRT_OPS 13
-#define ACOS_OPS 12
+#define ACOS_OPS 13
 
 /* Abramowitz and Stegun 4.4.46 coefficients a0..a7. */
 static const float AS0 = 1.5707963050f, AS1 = -0.2145988016f, AS2 = 0.0889789874f, AS3 = -0.0501743046f;
@@ -56,7 +56,7 @@ float orc32_rsqrt(float x) {
 
 float orc32_acos(float c) {
     const float a = fabsf(c);
-    const float s = sqrtf(1.0f - a);
+    const float s = sqrtf(fmaxf(1.0f - a, 0.0f)); /* |c| > 1 (rounding) gives acos(+-1) */
     float P = fmaf(AS7, a, AS6);
     P = fmaf(P, a, AS5);
     P = fmaf(P, a, AS4);
@@ -67,8 +67,6 @@ float orc32_acos(float c) {
     const float r = s * P;
     return c < 0.0f ? 3.14159265358979323846f - r : r;
 }
-
-static float clamp1(float c) { return fmaxf(fminf(c, 1.0f), -1.0f); }
 
 static uint64_t low_bits(int k) { return k >= 64 ? ~(uint64_t)0 : (((uint64_t)1 << k) - 1); }
 
@@ -125,6 +123,9 @@ int orc32_pixels(const orc_problem *pb, int n, const int32_t *xy, float *out0, f
     const float t0 = pb->thickness, kt = pb->thickness_slope;
     const float edge_hi = pb->hit_rule == 0 ? f_nb - 0.5f : nextafterf(f_nb, 0.0f);
     const float edge_lo = pb->hit_rule == 0 ? 0.5f : nextafterf(0.0f, 1.0f);
+    /* half a sector in radians (0 for the floor/ceil rule), its sine and cosine, FP64 rounded once */
+    const double del = pb->hit_rule == 0 ? M_PI / (2.0 * nb) : 0.0;
+    const float sdel = (float)sin(del), cdel = (float)cos(del);
 
     /* Direction table: cos, sin of (i + xi_phi) pi / N_d per noise class, FP64 rounded once. */
     float dcos[16][16], dsin[16][16];
@@ -204,12 +205,22 @@ int orc32_pixels(const orc_problem *pb, int n, const int32_t *xy, float *out0, f
                 const float rpn = orc32_rsqrt(pn2);
                 cg = nv * rpn;
                 sg = nsd * rpn;
-                gam = orc32_acos(clamp1(cg));
+                gam = orc32_acos(cg);
                 if (nsd < 0.0f) gam = -gam;
-                ops += RSQRT_OPS + 2 + 2 + ACOS_OPS + 2;
+                ops += RSQRT_OPS + 2 + ACOS_OPS + 2;
             }
             const float off = fmaf(-gam, K, half_nb);
-            ops += 2 + 2 + 3 + 3 + RSQRT_OPS + 3 + 6 + 2 + 1 + 1 + 2;
+            /* Cosine thresholds of the edge bands: a front direction whose cosine to v is below
+             * thr_p (side +omega) or thr_m (side -omega) lies within the band next to that side's
+             * hemisphere edge, i.e. at an angle from v above gamma + pi/2 - delta (side +) or
+             * pi/2 - gamma - delta (side -), delta = half a sector (0 for the floor/ceil rule).
+             * Angles outside [0, pi] give 2 (every direction) or -2 (none). */
+            const float cu_p = fmaf(cg, cdel, sg * sdel), su_p = fmaf(sg, cdel, -(cg * sdel));
+            const float cu_m = fmaf(cg, cdel, -(sg * sdel)), su_m = fmaf(sg, cdel, cg * sdel);
+            const float thr_p = cu_p >= 0.0f ? -su_p : (su_p < 0.0f ? 2.0f : -2.0f);
+            const float thr_m = cu_m >= 0.0f ? su_m : (su_m > 0.0f ? 2.0f : -2.0f);
+            const float thr2_p = thr_p * thr_p, thr2_m = thr_m * thr_m;
+            ops += 2 + 2 + 3 + 3 + RSQRT_OPS + 3 + 6 + 2 + 1 + 1 + 2 + 8 + 8 + 2;
 
             uint64_t b = 0;
             for (int side = 0; side < 2; ++side) {
@@ -217,6 +228,7 @@ int orc32_pixels(const orc_problem *pb, int n, const int32_t *xy, float *out0, f
                 const float wsx = pos ? cphi : -cphi, wsy = pos ? sphi : -sphi;
                 const float sK = pos ? K : -K;
                 const float edge = pos ? f_nb : 0.0f;
+                const float thr = pos ? thr_p : thr_m, thr2 = pos ? thr2_p : thr2_m;
                 for (int j = 0; j < ns; ++j) {
                     ++c_visit;
                     /* Step offset along the direction and the nearest pixel (ties to even). */
@@ -233,20 +245,26 @@ int orc32_pixels(const orc_problem *pb, int n, const int32_t *xy, float *out0, f
                     ops += 2 + 3;
                     if (!is_geometry(zq)) { ++c_skip; continue; }
 
-                    /* Front sample: l = s_f - p, its cosine to v, its sector coordinate. */
-                    const float uq = u + dxf, vq = v + dyf;
-                    const float aq = fmaf(uq, inv_fx, kx0), bq = fmaf(vq, ninv_fy, ky0);
+                    /* Front sample: l = s_f - p, its cosine to v, its sector coordinate.  The sample's
+                     * view ray is the centre pixel's ray plus the pixel offset over the focal length. */
+                    const float aq = fmaf(dxf, inv_fx, ax), bq = fmaf(dyf, ninv_fy, by);
                     const float lx = fmaf(aq, zq, -px), ly = fmaf(bq, zq, -py), lz = z - zq;
                     const float dv = fmaf(lx, vx, fmaf(ly, vy, lz * vz));
                     const float ll = fmaf(lx, lx, fmaf(ly, ly, lz * lz));
+                    ops += 2 + 3 + 6 + 6;
+                    /* Inside the edge band (cosine test on dv / sqrt(ll) against thr without the
+                     * square root): by the half-covered rule (Section 3.1) the sample occludes
+                     * nothing, because its back endpoint lies still closer to that edge. */
+                    {
+                        const float d2 = dv * dv, r2 = thr2 * ll;
+                        const int beyond = thr >= 0.0f ? (dv < 0.0f || d2 < r2) : (dv < 0.0f && d2 > r2);
+                        if (beyond) continue;
+                    }
                     const float rl = orc32_rsqrt(ll);
-                    const float cf = clamp1(dv * rl);
+                    const float cf = dv * rl;
                     const float Xf = fminf(fmaxf(fmaf(orc32_acos(cf), sK, off), 0.0f), f_nb);
-                    ops += 2 + 2 + 3 + 6 + RSQRT_OPS + 3 + ACOS_OPS + 3 + 1;
-                    /* The back endpoint is at or beyond the front one toward this side's edge, so a
-                     * front endpoint inside the edge band occludes no sector (Section 3.1 hit rule):
-                     * the band is half a sector for the half-covered rule, the edge itself for the
-                     * floor/ceil rule.  The sample ends here. */
+                    ops += RSQRT_OPS + 1 + ACOS_OPS + 3 + 1;
+                    /* The same band in sector units (exact for the computed endpoint). */
                     if (pos ? Xf > edge_hi : Xf < edge_lo) continue;
 
                     /* Back sample (constant thickness behind the front one). */
@@ -256,15 +274,17 @@ int orc32_pixels(const orc_problem *pb, int n, const int32_t *xy, float *out0, f
                     } else {
                         const float dvb = dv - tp;
                         const float llb = fmaf(m2t, dv, ll + t2);
-                        const float cb = clamp1(dvb * orc32_rsqrt(llb));
+                        const float cb = dvb * orc32_rsqrt(llb);
                         Xb = fminf(fmaxf(fmaf(orc32_acos(cb), sK, off), 0.0f), f_nb);
-                        ops += 3 + RSQRT_OPS + 3 + ACOS_OPS + 3;
+                        ops += 3 + RSQRT_OPS + 1 + ACOS_OPS + 3;
                     }
-                    const float A = fminf(Xf, Xb), B = fmaxf(Xf, Xb);
+                    /* The back endpoint lies toward this side's edge: [A, B] = [X_f, X_b] on side +,
+                     * [X_b, X_f] on side - (a rounding-level reversal leaves B < A: no sector). */
+                    const float A = pos ? Xf : Xb, B = pos ? Xb : Xf;
                     const uint64_t bj = orc32_sector_mask(A, B, nb, pb->hit_rule);
                     const int newly = __builtin_popcountll(bj & ~b);
                     b |= bj;
-                    ops += 2 + 12 + 3 + 1;
+                    ops += 12 + 3 + 1;
 
                     /* Indirect light from the newly occluded sectors (Section 3.3). */
                     if (newly > 0 && pb->gi) {

@@ -52,6 +52,7 @@ struct GatherParams {
     float inv_fx, inv_fy, kx0, ninv_fy, ky0;
     float Rfx, dn, K, half_nb, f_nb, inv_nb, inv_nd;
     float edge_hi, edge_lo;  // front endpoints beyond these occlude nothing (side +omega / -omega)
+    float sdel, cdel;        // sine and cosine of half a sector (0 and 1 for the floor/ceil rule)
     float t0, kt;
     float xi_s[16];
     float dcos[16][kMaxSlices];
@@ -65,7 +66,7 @@ struct GatherParams {
 // Abramowitz and Stegun 4.4.46: acos(x) = sqrt(1 - x) (a0 + a1 x + ... + a7 x^7), 0 <= x <= 1.
 __device__ __forceinline__ float own_acos(float c) {
     const float a = fabsf(c);
-    const float s = sqrtf(1.0f - a);
+    const float s = sqrtf(fmaxf(1.0f - a, 0.0f));  // |c| > 1 (rounding) gives acos(+-1)
     float P = fmaf(-0.0012624911f, a, 0.0066700901f);
     P = fmaf(P, a, -0.0170881256f);
     P = fmaf(P, a, 0.0308918810f);
@@ -91,8 +92,6 @@ __device__ __forceinline__ float own_rsqrt(float x) {
     }
     return y;
 }
-
-__device__ __forceinline__ float clamp1(float c) { return fmaxf(fminf(c, 1.0f), -1.0f); }
 
 // 1.5 * 2^23: adding it to |v| < 2^22 leaves round(v) in the low mantissa bits.
 constexpr float kMagic = 12582912.0f;
@@ -188,39 +187,47 @@ __device__ __forceinline__ Step make_step(const GatherParams &P, int x, int y, f
 
 // Per-pixel state the sample loop reads.
 struct Pixel {
-    float z, u, v, px, py, vx, vy, vz, tp, t2, m2t;
+    float z, ax, by, px, py, vx, vy, vz, tp, t2, m2t;
     float3 n;
 };
 
-template <int NB, bool F16, bool INF_T>
-__device__ __forceinline__ void process_step(const GatherParams &P, const Pixel &X, const Step &s, float sK,
-                                             float edge, float off, typename MaskT<NB>::T &b, float &GIr,
+// One sample of side POS (+omega when true): front and back endpoints, sector run, mask
+// update and indirect light.  thr/thr2: the side's edge-band cosine threshold and its square.
+template <int NB, bool F16, bool INF_T, bool POS>
+__device__ __forceinline__ void process_step(const GatherParams &P, const Pixel &X, const Step &s, float off,
+                                             float thr, float thr2, typename MaskT<NB>::T &b, float &GIr,
                                              float &GIg, float &GIb) {
     using M = typename MaskT<NB>::T;
     const float zq = s.zq;
-    // Front sample s_f, l = s_f - p, its cosine to v and its sector coordinate.
-    const float uq = X.u + s.dxf, vq = X.v + s.dyf;
-    const float aq = fmaf(uq, P.inv_fx, P.kx0), bq = fmaf(vq, P.ninv_fy, P.ky0);
+    // Front sample s_f (view ray of the sample pixel = the centre ray plus the pixel offset over
+    // the focal length), l = s_f - p, its cosine to v.
+    const float aq = fmaf(s.dxf, P.inv_fx, X.ax), bq = fmaf(s.dyf, P.ninv_fy, X.by);
     const float lx = fmaf(aq, zq, -X.px), ly = fmaf(bq, zq, -X.py), lz = X.z - zq;
     const float dv = fmaf(lx, X.vx, fmaf(ly, X.vy, lz * X.vz));
     const float ll = fmaf(lx, lx, fmaf(ly, ly, lz * lz));
+    // Inside this side's edge band (cosine dv/|l| below thr, tested without the square root):
+    // the back endpoint lies still closer to the edge, so no sector is half covered.
+    {
+        const float d2 = dv * dv, r2 = thr2 * ll;
+        const bool beyond = thr >= 0.0f ? (dv < 0.0f || d2 < r2) : (dv < 0.0f && d2 > r2);
+        if (beyond) return;
+    }
+    const float sK = POS ? P.K : -P.K;
     const float rl = own_rsqrt(ll);
-    const float Xf = fminf(fmaxf(fmaf(own_acos(clamp1(dv * rl)), sK, off), 0.0f), P.f_nb);
-    // The back endpoint lies at or beyond the front one toward this side's hemisphere edge, so
-    // a front endpoint within the edge band (half a sector for the half-covered rule, the edge
-    // itself for the floor/ceil rule) cannot occlude any sector: nothing more to do.
-    if (sK > 0.0f ? Xf > P.edge_hi : Xf < P.edge_lo) return;
+    const float Xf = fminf(fmaxf(fmaf(own_acos(dv * rl), sK, off), 0.0f), P.f_nb);
+    // the same band in sector units (half a sector for the half-covered rule, the edge for floor/ceil)
+    if (POS ? Xf > P.edge_hi : Xf < P.edge_lo) return;
     // Back sample, thickness t behind the front one along the centre pixel's view ray.
     float Xb;
     if (INF_T) {
-        Xb = edge;
+        Xb = POS ? P.f_nb : 0.0f;
     } else {
         const float dvb = dv - X.tp;
         const float llb = fmaf(X.m2t, dv, ll + X.t2);
-        const float cb = clamp1(dvb * own_rsqrt(llb));
-        Xb = fminf(fmaxf(fmaf(own_acos(cb), sK, off), 0.0f), P.f_nb);
+        Xb = fminf(fmaxf(fmaf(own_acos(dvb * own_rsqrt(llb)), sK, off), 0.0f), P.f_nb);
     }
-    const float A = fminf(Xf, Xb), B = fmaxf(Xf, Xb);
+    // [A, B]: the back endpoint lies toward this side's edge (a rounding-level reversal gives B < A).
+    const float A = POS ? Xf : Xb, B = POS ? Xb : Xf;
     const M bj = sector_run<NB>(A, B, P.hit_rule);
     const int newly = popc_(bj & ~b);
     b |= bj;
@@ -234,6 +241,21 @@ __device__ __forceinline__ void process_step(const GatherParams &P, const Pixel 
         GIr = fmaf(wgt, cj.x, GIr);
         GIg = fmaf(wgt, cj.y, GIg);
         GIb = fmaf(wgt, cj.z, GIb);
+    }
+}
+
+// Steps of one side, near to far.  Once a step leaves the screen every later step of that side
+// does too (the rounded offset is monotone in j), so the side ends there.
+template <int NB, bool F16, bool INF_T, int STEP_MODE, bool POS>
+__device__ __forceinline__ void march_side(const GatherParams &P, const Pixel &X, int x, int y, float xidn,
+                                           float rpx, float cphi, float sphi, float off, float thr, float thr2,
+                                           typename MaskT<NB>::T &b, float &GIr, float &GIg, float &GIb) {
+    const float wsx = POS ? cphi : -cphi, wsy = POS ? sphi : -sphi;
+#pragma unroll 2
+    for (int j = 0; j < P.ns; ++j) {
+        const Step st = make_step<STEP_MODE>(P, x, y, (float)(j + 1), xidn, rpx, wsx, wsy);
+        if (!st.on) break;
+        if (st.ok && is_geometry(st.zq)) process_step<NB, F16, INF_T, POS>(P, X, st, off, thr, thr2, b, GIr, GIg, GIb);
     }
 }
 
@@ -255,14 +277,14 @@ __device__ __forceinline__ void gather_pixel(const GatherParams &P, int x, int y
     // Pixel setup (Algorithm 1: p, n_p, projected radius, step size).
     Pixel X;
     X.z = z;
-    X.u = (float)x + 0.5f;
-    X.v = (float)y + 0.5f;
-    const float ax = fmaf(X.u, P.inv_fx, P.kx0), by = fmaf(X.v, P.ninv_fy, P.ky0);
-    X.px = ax * z;
-    X.py = by * z;
-    const float rd = own_rsqrt(fmaf(ax, ax, fmaf(by, by, 1.0f)));
-    X.vx = -(ax * rd);
-    X.vy = -(by * rd);
+    const float u = (float)x + 0.5f, v = (float)y + 0.5f;
+    X.ax = fmaf(u, P.inv_fx, P.kx0);
+    X.by = fmaf(v, P.ninv_fy, P.ky0);
+    X.px = X.ax * z;
+    X.py = X.by * z;
+    const float rd = own_rsqrt(fmaf(X.ax, X.ax, fmaf(X.by, X.by, 1.0f)));
+    X.vx = -(X.ax * rd);
+    X.vy = -(X.by * rd);
     X.vz = rd;
     X.n = load_xyz<F16>(P.normal, P.normal_pitch, x, y);
     const float rpx = fminf(P.Rfx / z, 1048576.0f);
@@ -293,26 +315,24 @@ __device__ __forceinline__ void gather_pixel(const GatherParams &P, int x, int y
             const float rpn = own_rsqrt(pn2);
             cg = nv * rpn;
             sg = nsd * rpn;
-            gam = own_acos(clamp1(cg));
+            gam = own_acos(cg);
             if (nsd < 0.0f) gam = -gam;
         }
         const float off = fmaf(-gam, P.K, P.half_nb);
+        // Edge-band cosine thresholds: a front direction at an angle from v above
+        // gamma + pi/2 - delta (side +) or pi/2 - gamma - delta (side -), delta = half a sector
+        // (0 for the floor/ceil rule), lies in the band; angles outside [0, pi] give 2 (all) or -2 (none).
+        const float cu_p = fmaf(cg, P.cdel, sg * P.sdel), su_p = fmaf(sg, P.cdel, -(cg * P.sdel));
+        const float cu_m = fmaf(cg, P.cdel, -(sg * P.sdel)), su_m = fmaf(sg, P.cdel, cg * P.sdel);
+        const float thr_p = cu_p >= 0.0f ? -su_p : (su_p < 0.0f ? 2.0f : -2.0f);
+        const float thr_m = cu_m >= 0.0f ? su_m : (su_m > 0.0f ? 2.0f : -2.0f);
 
         M b = 0;
-        // Side -omega, then side +omega, near to far.  Once a step leaves the screen every later
-        // step of that side does too (the rounded offset is monotone in j), so the side ends there.
-#pragma unroll 1
-        for (int side = 0; side < 2; ++side) {
-            const float sgn = side ? 1.0f : -1.0f;
-            const float wsx = sgn * cphi, wsy = sgn * sphi, sK = sgn * P.K;
-            const float edge = side ? P.f_nb : 0.0f;
-#pragma unroll 2
-            for (int j = 0; j < P.ns; ++j) {
-                const Step st = make_step<STEP_MODE>(P, x, y, (float)(j + 1), xidn, rpx, wsx, wsy);
-                if (!st.on) break;
-                if (st.ok && is_geometry(st.zq)) process_step<NB, F16, INF_T>(P, X, st, sK, edge, off, b, GIr, GIg, GIb);
-            }
-        }
+        // Side -omega, then side +omega (Section 3.3: nearer samples occlude later ones first).
+        march_side<NB, F16, INF_T, STEP_MODE, false>(P, X, x, y, xidn, rpx, cphi, sphi, off, thr_m, thr_m * thr_m, b,
+                                                     GIr, GIg, GIb);
+        march_side<NB, F16, INF_T, STEP_MODE, true>(P, X, x, y, xidn, rpx, cphi, sphi, off, thr_p, thr_p * thr_p, b,
+                                                    GIr, GIg, GIb);
 
         // Slice end: unoccluded fraction, then the ambient cones (Section 3.2).
         AO += (float)(NB - popc_(b)) * P.inv_nb;

@@ -167,6 +167,9 @@ void fill_params(ssilvb::GatherParams &P, const ssilvb_gbuffer *g, const ssilvb_
     P.inv_nd = 1.0f / (float)nd;
     P.edge_hi = p->hit_rule == 0 ? P.f_nb - 0.5f : std::nextafter(P.f_nb, 0.0f);
     P.edge_lo = p->hit_rule == 0 ? 0.5f : std::nextafter(0.0f, 1.0f);
+    const double del = p->hit_rule == 0 ? M_PI / (2.0 * nb) : 0.0;
+    P.sdel = (float)std::sin(del);
+    P.cdel = (float)std::cos(del);
     P.t0 = p->thickness;
     P.kt = p->thickness_slope;
     for (int cl = 0; cl < 16; ++cl) {
