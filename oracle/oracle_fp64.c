@@ -210,9 +210,15 @@ int orc64_pixels(const orc_problem *pb, int n, const int32_t *xy, double *out0, 
                 for (int j = 0; j < ns; ++j) {
                     /* Which pixel this step reads (binary32, nearest pixel, ties to even). */
                     const float jp1 = (float)(j + 1);
-                    const float uj = fmaf(jp1, dn, xidn);
-                    const float off = pb->step_mode == 0 ? uj * rpx : (uj * uj) * rpx;
-                    const float dxf = rintf(off * wsx), dyf = rintf(off * wsy);
+                    float off;
+                    if (pb->step_mode == 0) {
+                        off = fmaf(jp1, rpx * dn, (xi_s * dn) * rpx);
+                    } else {
+                        const float uj = fmaf(jp1, dn, xidn);
+                        off = (uj * uj) * rpx;
+                    }
+                    const float dxf = fmaf(off, wsx, 12582912.0f) - 12582912.0f;
+                    const float dyf = fmaf(off, wsy, 12582912.0f) - 12582912.0f;
                     if (dxf == 0.0f && dyf == 0.0f) continue;
                     const int qx = x + (int)dxf, qy = y + (int)dyf;
                     if (qx < 0 || qy < 0 || qx >= W || qy >= H) continue;

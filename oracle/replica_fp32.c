@@ -177,6 +177,7 @@ int orc32_pixels(const orc_problem *pb, int n, const int32_t *xy, float *out0, f
         const int cls = (y & 3) * 4 + (x & 3);
         const float xi_s = pb->noise ? pb->noise[2 * cls + 1] : 0.0f;
         const float xidn = xi_s * dn;
+        const float del = rpx * dn, xdel = xidn * rpx; /* step unit r/(N_s+1) and its jitter */
         float tp = 0.0f, t2 = 0.0f, m2t = 0.0f;
         if (!inf_t) {
             tp = fmaf(kt, z, t0);
@@ -232,10 +233,17 @@ int orc32_pixels(const orc_problem *pb, int n, const int32_t *xy, float *out0, f
                 for (int j = 0; j < ns; ++j) {
                     ++c_visit;
                     /* Step offset along the direction and the nearest pixel (ties to even). */
-                    const float uj = fmaf((float)(j + 1), dn, xidn);
-                    const float o = pb->step_mode == 0 ? uj * rpx : (uj * uj) * rpx;
-                    const float dxf = rintf(o * wsx), dyf = rintf(o * wsy);
-                    ops += 2 + (pb->step_mode != 0) + 4 + 3;
+                    float o;
+                    if (pb->step_mode == 0) {
+                        o = fmaf((float)(j + 1), del, xdel);
+                    } else {
+                        const float uj = fmaf((float)(j + 1), dn, xidn);
+                        o = (uj * uj) * rpx;
+                    }
+                    /* nearest integer (ties to even) of the exact product, via a fused add of 1.5*2^23 */
+                    const float dxf = fmaf(o, wsx, 12582912.0f) - 12582912.0f;
+                    const float dyf = fmaf(o, wsy, 12582912.0f) - 12582912.0f;
+                    ops += 1 + 2 * (pb->step_mode != 0) + 4 + 3;
                     if (dxf == 0.0f && dyf == 0.0f) { ++c_skip; continue; }
                     const int qx = x + (int)dxf, qy = y + (int)dyf;
                     ops += 4 + 3;

@@ -166,30 +166,46 @@ struct Step {
     bool ok;         // on screen and not the centre pixel
 };
 
+struct Pixel;
 template <int STEP_MODE>
-__device__ __forceinline__ Step make_step(const GatherParams &P, int x, int y, float jf, float xidn, float rpx,
-                                          float wsx, float wsy) {
+__device__ __forceinline__ Step make_step(const GatherParams &P, const Pixel &X, int x, int y, float jf, float wsx,
+                                          float wsy);
+
+// Per-pixel state the sample loop reads.
+struct Pixel {
+    float z, ax, by, px, py, vx, vy, vz, tp, t2, m2t;
+    float del, xdel;  // step unit r/(N_s+1) and the jitter xi_s times it (constant steps)
+    float dn_, xidn, rpx;  // quadratic steps: 1/(N_s+1), xi_s/(N_s+1), r
+    int qx0, qy0;     // x, y minus the bit pattern of 1.5*2^23
+    float3 n;
+};
+
+// Offset of step j (jf = j + 1) along the direction, r (jf + xi_s)/(N_s + 1) or its quadratic
+// form, and its nearest pixel: fma(o, w, 1.5*2^23) rounds o*w to the nearest integer (ties to
+// even) in the low mantissa bits, so qx = bits - (0x4B400000 - x).
+template <int STEP_MODE>
+__device__ __forceinline__ Step make_step(const GatherParams &P, const Pixel &X, int x, int y, float jf, float wsx,
+                                          float wsy) {
     Step s;
-    const float uj = fmaf(jf, P.dn, xidn);
-    const float o = STEP_MODE == 0 ? uj * rpx : (uj * uj) * rpx;
-    const float rx = o * wsx + kMagic, ry = o * wsy + kMagic;
-    const int dx = __float_as_int(rx) - kMagicBits, dy = __float_as_int(ry) - kMagicBits;
+    float o;
+    if (STEP_MODE == 0) {
+        o = fmaf(jf, X.del, X.xdel);
+    } else {
+        const float uj = fmaf(jf, X.dn_, X.xidn);
+        o = (uj * uj) * X.rpx;
+    }
+    const float rx = fmaf(o, wsx, kMagic), ry = fmaf(o, wsy, kMagic);
     s.dxf = rx - kMagic;
     s.dyf = ry - kMagic;
-    s.qx = x + dx;
-    s.qy = y + dy;
+    s.qx = __float_as_int(rx) + X.qx0;
+    s.qy = __float_as_int(ry) + X.qy0;
     s.on = (unsigned)s.qx < (unsigned)P.W && (unsigned)s.qy < (unsigned)P.H;
-    s.ok = s.on && ((dx | dy) != 0);
+    s.ok = s.on && ((s.qx != x) | (s.qy != y));
     s.zq = 0.0f;
     if (s.ok) s.zq = __ldg(P.depth + (unsigned)s.qy * (unsigned)P.depth_pitch + (unsigned)s.qx);
     return s;
 }
 
-// Per-pixel state the sample loop reads.
-struct Pixel {
-    float z, ax, by, px, py, vx, vy, vz, tp, t2, m2t;
-    float3 n;
-};
 
 // One sample of side POS (+omega when true): front and back endpoints, sector run, mask
 // update and indirect light.  thr/thr2: the side's edge-band cosine threshold and its square.
@@ -247,13 +263,13 @@ __device__ __forceinline__ void process_step(const GatherParams &P, const Pixel 
 // Steps of one side, near to far.  Once a step leaves the screen every later step of that side
 // does too (the rounded offset is monotone in j), so the side ends there.
 template <int NB, bool F16, bool INF_T, int STEP_MODE, bool POS>
-__device__ __forceinline__ void march_side(const GatherParams &P, const Pixel &X, int x, int y, float xidn,
-                                           float rpx, float cphi, float sphi, float off, float thr, float thr2,
+__device__ __forceinline__ void march_side(const GatherParams &P, const Pixel &X, int x, int y, float cphi,
+                                           float sphi, float off, float thr, float thr2,
                                            typename MaskT<NB>::T &b, float &GIr, float &GIg, float &GIb) {
     const float wsx = POS ? cphi : -cphi, wsy = POS ? sphi : -sphi;
 #pragma unroll 2
     for (int j = 0; j < P.ns; ++j) {
-        const Step st = make_step<STEP_MODE>(P, x, y, (float)(j + 1), xidn, rpx, wsx, wsy);
+        const Step st = make_step<STEP_MODE>(P, X, x, y, (float)(j + 1), wsx, wsy);
         if (!st.on) break;
         if (st.ok && is_geometry(st.zq)) process_step<NB, F16, INF_T, POS>(P, X, st, off, thr, thr2, b, GIr, GIg, GIb);
     }
@@ -290,6 +306,13 @@ __device__ __forceinline__ void gather_pixel(const GatherParams &P, int x, int y
     const float rpx = fminf(P.Rfx / z, 1048576.0f);
     const int cls = (y & 3) * 4 + (x & 3);
     const float xidn = P.xi_s[cls] * P.dn;
+    X.del = rpx * P.dn;
+    X.xdel = xidn * rpx;
+    X.dn_ = P.dn;
+    X.xidn = xidn;
+    X.rpx = rpx;
+    X.qx0 = x - kMagicBits;
+    X.qy0 = y - kMagicBits;
     X.tp = X.t2 = X.m2t = 0.0f;
     if (!INF_T) {
         X.tp = fmaf(P.kt, z, P.t0);
@@ -329,9 +352,9 @@ __device__ __forceinline__ void gather_pixel(const GatherParams &P, int x, int y
 
         M b = 0;
         // Side -omega, then side +omega (Section 3.3: nearer samples occlude later ones first).
-        march_side<NB, F16, INF_T, STEP_MODE, false>(P, X, x, y, xidn, rpx, cphi, sphi, off, thr_m, thr_m * thr_m, b,
+        march_side<NB, F16, INF_T, STEP_MODE, false>(P, X, x, y, cphi, sphi, off, thr_m, thr_m * thr_m, b,
                                                      GIr, GIg, GIb);
-        march_side<NB, F16, INF_T, STEP_MODE, true>(P, X, x, y, xidn, rpx, cphi, sphi, off, thr_p, thr_p * thr_p, b,
+        march_side<NB, F16, INF_T, STEP_MODE, true>(P, X, x, y, cphi, sphi, off, thr_p, thr_p * thr_p, b,
                                                     GIr, GIg, GIb);
 
         // Slice end: unoccluded fraction, then the ambient cones (Section 3.2).
@@ -392,7 +415,7 @@ __global__ void __launch_bounds__(256) gather_tile_kernel(const __grid_constant_
 // slice directions and step offsets: their samples land on neighbouring pixels and the
 // depth gathers of a warp touch a few cache lines instead of one per lane.
 #ifndef SSILVB_CLASS_MIN_BLOCKS
-#define SSILVB_CLASS_MIN_BLOCKS 5
+#define SSILVB_CLASS_MIN_BLOCKS 10
 #endif
 template <int NB, bool F16, bool INF_T, int STEP_MODE>
 __global__ void __launch_bounds__(128, SSILVB_CLASS_MIN_BLOCKS) gather_class_kernel(const __grid_constant__ GatherParams P) {

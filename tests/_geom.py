@@ -15,13 +15,15 @@ def f32(x):
 
 def sample_offsets(radius, fx, z, ns, step_mode=0):
     """Offsets (pixels) of the N_s steps, in binary32 as the sample pixel is chosen (xi_s = 0)."""
-    rpx = min(f32(f32(radius) * f32(fx)) / f32(z), f32(1048576.0))
-    rpx = f32(rpx)
+    rpx = f32(min(f32(f32(radius) * f32(fx)) / f32(z), f32(1048576.0)))
     dn = f32(f32(1.0) / f32(ns + 1))
     out = []
     for j in range(ns):
-        uj = f32(f32(j + 1) * dn)
-        out.append(f32(uj * rpx) if step_mode == 0 else f32(f32(uj * uj) * rpx))
+        if step_mode == 0:
+            out.append(f32(f32(j + 1) * f32(rpx * dn)))
+        else:
+            uj = f32(f32(j + 1) * dn)
+            out.append(f32(f32(uj * uj) * rpx))
     return out
 
 
@@ -62,8 +64,9 @@ def sample_pixels(x, y, W, H, depth, offs, cphi, sphi, sigma):
     """(qx, qy) of the steps that read geometry, near to far, for one side."""
     out = []
     for o in offs:
-        dx = float(np.rint(f32(o * f32(sigma * cphi))))
-        dy = float(np.rint(f32(o * f32(sigma * sphi))))
+        # nearest integer (ties to even) of the exact binary32 product
+        dx = float(np.rint(float(o) * float(f32(sigma * cphi))))
+        dy = float(np.rint(float(o) * float(f32(sigma * sphi))))
         if dx == 0 and dy == 0:
             continue
         qx, qy = x + int(dx), y + int(dy)
