@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ssilvb", choices=["ssilvb", "reference"])
-    ap.add_argument("--workload", default="4k", choices=["4k", "1080p", "256"])
+    ap.add_argument("--workload", default="4k", choices=["4k", "1080p", "256", "batch"])
     ap.add_argument("--nb", type=int, default=32)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -203,11 +203,108 @@ def run_reference(args, world, rank):
     print(json.dumps(out))
 
 
+def batch_workload(n_frames=64, base_seed=1000):
+    """64 seeded frames of uneven sizes (640x360 .. 2560x1440), per-frame N_d 1-4, N_s 8-32,
+    t 0.1-1.0 m; 64 spheres + 16 panels, FP32 storage, N_b 32, R 2 m, 4x4 IGN noise."""
+    out = []
+    for seed, W, H, nd, ns, t in scenegen.batch_recipe(n_frames, base_seed):
+        g = scenegen.render(seed, W, H, 64, 16)
+        out.append((g, scenegen.Params(nd, ns, 2.0, t)))
+    return out
+
+
+def run_batch_bench(args, world, rank, local):
+    import torch
+
+    import paper_2301_11376_gb300 as ssilvb
+    ssilvb.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    frames_np = batch_workload(64, 1000 + 64 * rank)
+    noise = scenegen.ign_table()
+    ctx = ssilvb.Context(local)
+    stream = torch.cuda.current_stream(dev)
+    frames, keep, hold = [], None, []
+    samples = 0
+    for g, prm in frames_np:
+        H, W = g.depth.shape
+        d = torch.from_numpy(g.depth).to(dev)
+        n = torch.from_numpy(g.normal).to(dev)
+        r = torch.from_numpy(g.radiance).to(dev)
+        o0, _, _ = ssilvb.alloc_outputs(H, W, prm, dev)
+        f, keep = ctx.frame(d, n, r, g.camera, prm, o0, None, None, noise=noise, keep=keep)
+        frames.append(f)
+        hold.append((d, n, r, o0, g, prm))
+        samples += H * W * 2 * prm.num_slices * prm.steps_per_side
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    tuned = ctx.autotune(frames, stream)
+
+    def timed(fn, steps):
+        ts = []
+        for i in range(steps):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return ts
+
+    def batched():
+        ctx.gather_batch(frames, stream)
+
+    def plain_nosync():
+        for d, n, r, o0, g, prm in hold:
+            ctx.gather(d, n, r, g.camera, prm, o0, None, None, noise=noise, stream=stream)
+
+    def plain_sync():
+        for d, n, r, o0, g, prm in hold:
+            ctx.gather(d, n, r, g.camera, prm, o0, None, None, noise=noise, stream=stream)
+            stream.synchronize()
+
+    for fn in (batched, plain_nosync, plain_sync):
+        timed(fn, args.warmup)
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(world)
+    tb = timed(batched, args.steps)
+    barrier(world)
+    clk = clocks.stop()
+    tp = timed(plain_nosync, max(3, args.steps // 2))
+    ts_ = timed(plain_sync, max(3, args.steps // 2))
+    t_dev = max_over_ranks(world, sum(tb) / 1e3)
+    value = world * args.steps * samples / t_dev / 1e9
+    ms = t_dev / args.steps * 1e3
+    if rank != 0:
+        return
+    med = lambda v: statistics.median(v)
+    out = {"metric": "Gsamples/s (batched frames/s vs plain per-frame launch)", "value": value, "unit": "Gsamples/s",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "batch of 64 uneven frames (640x360..2560x1440), N_d 1-4, N_s 8-32, t 0.1-1.0, "
+                                  "fp32, nb32", "samples_per_step": samples,
+                      "l2": "flushed (256 MB write) between timed steps",
+                      "tuning": {"occupancy": tuned.occupancy, "rows_per_tile": tuned.rows_per_tile,
+                                 "use_graph": tuned.use_graph, "batch_mode": tuned.batch_mode}},
+           "frames_per_s": 64 * world / (t_dev / args.steps),
+           "plain_per_frame_launch": {"ms_per_batch_no_sync": med(tp), "ms_per_batch_host_sync": med(ts_),
+                                      "frames_per_s_no_sync": 64 / (med(tp) / 1e3),
+                                      "frames_per_s_host_sync": 64 / (med(ts_) / 1e3)},
+           "speedup_vs_plain_no_sync": med(tp) / med(tb), "speedup_vs_plain_host_sync": med(ts_) / med(tb),
+           "clocks": clk, "gpu_launches": args.steps}
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     world, rank, local = dist_init()
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.workload == "batch":
+        run_batch_bench(args, world, rank, local)
         return
     import torch
 

@@ -118,7 +118,9 @@ typedef struct {
     void *masks;
 } ssilvb_output;
 
-/* Launch choices that do not change any result (every choice gives bit-identical output). */
+/* Launch choices.  None of them changes any result: every choice gives bit-identical output.
+ * A zero field means "automatic": the autotuner's choice for this kind of call if
+ * ssilvb_autotune has run, else the library default. */
 typedef enum {
     SSILVB_MAP_AUTO = 0,  /* library default */
     SSILVB_MAP_TILE = 1,  /* one thread per pixel, 32 x 8 pixel tiles */
@@ -126,9 +128,24 @@ typedef enum {
 } ssilvb_mapping;
 
 typedef struct {
-    int mapping;          /* ssilvb_mapping */
-    int reserved[7];      /* must be zero */
+    int mapping;          /* ssilvb_mapping, single-frame calls */
+    int occupancy;        /* 0, or 8 / 10: blocks of 128 threads per SM the register budget is sized for */
+    int rows_per_tile;    /* batch: 0, or 1..8 image rows per work item */
+    int ctas_per_sm;      /* batch: 0 (as many as fit), or 1..16 blocks per SM in the persistent grid */
+    int use_graph;        /* batch, persistent mode: 0 auto, 1 launch through a cached CUDA graph, 2 plain */
+    int batch_mode;       /* batch: 0 auto, 1 one persistent kernel over a tile queue,
+                             2 one CUDA graph of independent per-frame kernels */
+    int reserved[2];      /* must be zero */
 } ssilvb_tuning;
+
+/* One frame of a batch: its G-buffer, camera, parameters and outputs, with the same meaning
+ * and rules as the arguments of ssilvb_gather. */
+typedef struct {
+    ssilvb_gbuffer gbuffer;
+    ssilvb_camera camera;
+    ssilvb_params params;
+    ssilvb_output out;
+} ssilvb_frame;
 
 /* Library version, major * 10000 + minor * 100 + patch. */
 int ssilvb_version(void);
@@ -163,6 +180,29 @@ ssilvb_status ssilvb_gather(ssilvb_ctx *ctx, const ssilvb_gbuffer *gbuffer, cons
 ssilvb_status ssilvb_gather_host(ssilvb_ctx *ctx, const ssilvb_gbuffer *gbuffer, const ssilvb_camera *camera,
                                  const ssilvb_params *params, const ssilvb_output *out,
                                  struct CUstream_st *stream);
+
+/* The gather over many frames of uneven sizes in ONE persistent launch (Algorithm 1 per pixel
+ * of every frame).  All frames must share sector_count, the storage format of normal and
+ * radiance, step_mode, and whether the thickness is infinite (else UNSUPPORTED); every other parameter,
+ * the size, the camera and the noise may differ per frame.  Output regions of different frames
+ * must not overlap.  Each frame's results are bit-identical to an ssilvb_gather of that frame.
+ * Two launch forms (ssilvb_tuning.batch_mode; the autotuner picks): (1) one persistent kernel:
+ * work items are bands of rows_per_tile rows x 128 pixels, concatenated over the frames and
+ * handed to the resident blocks through a queue counter the context owns, launched through a
+ * CUDA graph the context caches; (2) one CUDA graph whose independent nodes are the frames'
+ * kernels, so the frames run concurrently.  Asynchronous on stream.  The context keeps up to 4
+ * batches in flight; a call that needs a busy slot first waits on the host for that slot's
+ * previous batch.  1 <= n_frames <= 4096; frames is host memory read during the call. */
+ssilvb_status ssilvb_gather_batch(ssilvb_ctx *ctx, const ssilvb_frame *frames, int n_frames,
+                                  struct CUstream_st *stream);
+
+/* Autotuner: times the launch choices (register budget, rows per work item, CUDA graph or not;
+ * for n_frames == 1 also the single-frame mapping) on these frames, synchronising stream, and
+ * remembers the fastest for calls of the same kind (sector count, storage, thickness mode,
+ * pixel-count class, largest N_d and N_s, single or batch).  The frames' outputs are written
+ * (valid results).  *chosen (may be NULL) receives the winner. */
+ssilvb_status ssilvb_autotune(ssilvb_ctx *ctx, const ssilvb_frame *frames, int n_frames, struct CUstream_st *stream,
+                              ssilvb_tuning *chosen);
 
 /* Set the context's launch choices for later calls (copied).  INVALID_ARG on an unknown value. */
 ssilvb_status ssilvb_set_tuning(ssilvb_ctx *ctx, const ssilvb_tuning *tuning);

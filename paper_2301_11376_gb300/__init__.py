@@ -37,21 +37,39 @@ def _sources():
     return [os.path.join(_CSRC, f) for f in sorted(os.listdir(_CSRC))] + [os.path.join(INCLUDE, "ssilvb.h")]
 
 
+UNITS = ["ssilvb.cu", "batch.cu", "launch_nb32.cu", "launch_nb64.cu"]
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile the CUDA library in-tree for sm_103a with nvcc (no GPU needed)."""
+    """Compile the CUDA library in-tree for sm_103a with nvcc (no GPU needed): each
+    translation unit in parallel, then one shared library."""
+    from concurrent.futures import ThreadPoolExecutor
     os.makedirs(_BUILD, exist_ok=True)
     srcs = _sources()
     if not force and os.path.exists(LIB_PATH) and all(os.path.getmtime(LIB_PATH) >= os.path.getmtime(s) for s in srcs):
         return LIB_PATH
-    tmp = LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["nvcc", *NVCC_FLAGS, "-I" + INCLUDE, "-shared", "-o", tmp, os.path.join(_CSRC, "ssilvb.cu")]
-    if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    r = subprocess.run(cmd, capture_output=True, text=True)
+    tag = f".{os.getpid()}"
+    extra = ["-Xptxas=-v"] if verbose else []
+
+    def compile_unit(u):
+        obj = os.path.join(_BUILD, u.replace(".cu", tag + ".o"))
+        cmd = ["nvcc", *NVCC_FLAGS, *extra, "-I" + INCLUDE, "-c", "-o", obj, os.path.join(_CSRC, u)]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed on {u}:\n" + r.stdout + r.stderr)
+        return obj, r.stdout + r.stderr
+
+    with ThreadPoolExecutor(len(UNITS)) as ex:
+        results = list(ex.map(compile_unit, UNITS))
+    tmp = LIB_PATH.replace(".so", tag + ".so")
+    r = subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-o", tmp,
+                        *[o for o, _ in results]], capture_output=True, text=True)
+    for o, _ in results:
+        os.remove(o)
     if r.returncode != 0:
-        raise RuntimeError("nvcc failed:\n" + r.stdout + r.stderr)
+        raise RuntimeError("nvcc link failed:\n" + r.stdout + r.stderr)
     os.replace(tmp, LIB_PATH)
-    return r.stdout + r.stderr if verbose else LIB_PATH
+    return "".join(log for _, log in results) if verbose else LIB_PATH
 
 
 class Gbuffer(ctypes.Structure):
@@ -76,6 +94,16 @@ class ParamsC(ctypes.Structure):
 class Output(ctypes.Structure):
     _fields_ = [("out0", ctypes.c_void_p), ("out0_pitch", ctypes.c_size_t), ("out1", ctypes.c_void_p),
                 ("out1_pitch", ctypes.c_size_t), ("masks", ctypes.c_void_p)]
+
+
+class Frame(ctypes.Structure):
+    _fields_ = [("gbuffer", Gbuffer), ("camera", CameraC), ("params", ParamsC), ("out", Output)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("mapping", ctypes.c_int), ("occupancy", ctypes.c_int), ("rows_per_tile", ctypes.c_int),
+                ("ctas_per_sm", ctypes.c_int), ("use_graph", ctypes.c_int), ("batch_mode", ctypes.c_int),
+                ("reserved", ctypes.c_int * 2)]
 
 
 _lib = None
@@ -106,6 +134,12 @@ def load():
         f.restype = ctypes.c_int
     lib.ssilvb_synchronize.argtypes = [vp, vp]
     lib.ssilvb_synchronize.restype = ctypes.c_int
+    lib.ssilvb_set_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
+    lib.ssilvb_set_tuning.restype = ctypes.c_int
+    lib.ssilvb_gather_batch.argtypes = [vp, ctypes.POINTER(Frame), ctypes.c_int, vp]
+    lib.ssilvb_gather_batch.restype = ctypes.c_int
+    lib.ssilvb_autotune.argtypes = [vp, ctypes.POINTER(Frame), ctypes.c_int, vp, ctypes.POINTER(Tuning)]
+    lib.ssilvb_autotune.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -254,6 +288,41 @@ class Context:
         self._check(self.lib.ssilvb_gather_host(self.handle, ctypes.byref(g), ctypes.byref(_camera_c(camera)),
                                                 ctypes.byref(pc), ctypes.byref(o), ctypes.c_void_p(sh_)))
         del np
+
+    def frame(self, depth, normal, radiance, camera, params, out0, out1=None, masks=None, noise=None, sh=None,
+              keep=None):
+        """An ssilvb_frame for gather_batch from device tensors (host arrays kept alive in `keep`)."""
+        H, W = depth.shape
+        keep = keep if keep is not None else _HostArrays()
+        f = Frame()
+        f.gbuffer = Gbuffer(W, H, depth.data_ptr(), _pitch(depth, 1), normal.data_ptr(), _pitch(normal, 4),
+                            _fmt(normal), radiance.data_ptr(), _pitch(radiance, 4), _fmt(radiance))
+        f.camera = _camera_c(camera)
+        f.params = _params_c(params, keep, noise, sh)
+        f.out = Output(out0.data_ptr(), _pitch(out0, 4), out1.data_ptr() if out1 is not None else None,
+                       _pitch(out1, 4) if out1 is not None else 0, masks.data_ptr() if masks is not None else None)
+        return f, keep
+
+    def gather_batch(self, frames, stream=None):
+        """ssilvb_gather_batch over a list of Frame structs (see frame())."""
+        import torch
+        arr = (Frame * len(frames))(*frames)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self._check(self.lib.ssilvb_gather_batch(self.handle, arr, len(frames), ctypes.c_void_p(s.cuda_stream)))
+
+    def autotune(self, frames, stream=None):
+        """ssilvb_autotune over a list of Frame structs; returns the chosen Tuning."""
+        import torch
+        arr = (Frame * len(frames))(*frames)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        t = Tuning()
+        self._check(self.lib.ssilvb_autotune(self.handle, arr, len(frames), ctypes.c_void_p(s.cuda_stream),
+                                             ctypes.byref(t)))
+        return t
+
+    def set_tuning(self, mapping=0, occupancy=0, rows_per_tile=0, ctas_per_sm=0, use_graph=0, batch_mode=0):
+        t = Tuning(mapping, occupancy, rows_per_tile, ctas_per_sm, use_graph, batch_mode)
+        self._check(self.lib.ssilvb_set_tuning(self.handle, ctypes.byref(t)))
 
     def synchronize(self, stream=None):
         self._check(self.lib.ssilvb_synchronize(self.handle, ctypes.c_void_p(stream.cuda_stream if stream else None)))

@@ -412,18 +412,76 @@ __global__ void __launch_bounds__(256) gather_tile_kernel(const __grid_constant_
 
 // Class-strided mapping: a block covers 128 consecutive pixels of one row; warp w takes the
 // pixels with x = 4 * lane + w, so all 32 lanes share a 4x4 noise class and therefore the
-// slice directions and step offsets: their samples land on neighbouring pixels and the
-// depth gathers of a warp touch a few cache lines instead of one per lane.
-#ifndef SSILVB_CLASS_MIN_BLOCKS
-#define SSILVB_CLASS_MIN_BLOCKS 10
-#endif
-template <int NB, bool F16, bool INF_T, int STEP_MODE>
-__global__ void __launch_bounds__(128, SSILVB_CLASS_MIN_BLOCKS) gather_class_kernel(const __grid_constant__ GatherParams P) {
+// slice directions and step offsets: their samples land on neighbouring pixels and their
+// skip decisions agree.  MINB: blocks of 128 threads per SM the register budget is sized for.
+template <int NB, bool F16, bool INF_T, int STEP_MODE, int MINB>
+__global__ void __launch_bounds__(128, MINB) gather_class_kernel(const __grid_constant__ GatherParams P) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int x = blockIdx.x * 128 + 4 * lane + w;
     const int y = blockIdx.y;
     if (x >= P.W) return;
     gather_pixel<NB, F16, INF_T, STEP_MODE>(P, x, y);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Batched form: many frames of different sizes and parameters in one persistent launch.
+// The work list is the concatenation of every frame's tiles (tiles_x = ceil(W/128) tiles per
+// band of `rows` rows, bands top to bottom).  Each block takes the next tile from a queue
+// counter in global memory; tiles are handed out in order, so a block's frame index only moves
+// forward and the frame's parameters are copied to shared memory once per frame change.
+struct FrameDesc {
+    GatherParams P;
+    int tile_begin;  // global index of the frame's first tile
+    int tiles_x;     // tiles per band
+    int rows;        // rows per tile
+    int pad;
+};
+
+struct BatchHeader {
+    int n_frames;
+    int total_tiles;
+    int pad[2];
+};
+
+template <int NB, bool F16, bool INF_T, int STEP_MODE, int MINB>
+__global__ void __launch_bounds__(128, MINB)
+    gather_batch_kernel(const BatchHeader *__restrict__ hdr, const FrameDesc *__restrict__ frames,
+                        unsigned *__restrict__ queue) {
+    __shared__ GatherParams sP;
+    __shared__ int s_tile, s_frame;
+    const int n_frames = hdr->n_frames, total = hdr->total_tiles;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int cur = -1;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int t = (int)atomicAdd(queue, 1u);
+            int f = cur < 0 ? 0 : cur;
+            if (t < total)
+                while (f + 1 < n_frames && __ldg(&frames[f + 1].tile_begin) <= t) ++f;
+            s_tile = t;
+            s_frame = f;
+        }
+        __syncthreads();
+        const int t = s_tile, f = s_frame;
+        if (t >= total) break;
+        if (f != cur) {
+            const int *src = reinterpret_cast<const int *>(&frames[f].P);
+            int *dst = reinterpret_cast<int *>(&sP);
+            for (int k = threadIdx.x; k < (int)(sizeof(GatherParams) / 4); k += blockDim.x) dst[k] = __ldg(src + k);
+            cur = f;
+            __syncthreads();
+        }
+        const int local = t - __ldg(&frames[f].tile_begin);
+        const int tx = __ldg(&frames[f].tiles_x), rows = __ldg(&frames[f].rows);
+        const int band = local / tx, xb = local - band * tx;
+        const int x = xb * 128 + 4 * lane + w;
+        for (int r = 0; r < rows; ++r) {
+            const int y = band * rows + r;
+            if (y >= sP.H) break;
+            if (x < sP.W) gather_pixel<NB, F16, INF_T, STEP_MODE>(sP, x, y);
+        }
+        __syncthreads();  // everyone is done with s_tile, s_frame and sP before they change
+    }
 }
 
 }  // namespace ssilvb

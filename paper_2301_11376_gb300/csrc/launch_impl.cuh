@@ -1,0 +1,99 @@
+// Launch wrappers for one sector count (included by launch_nb32.cu and launch_nb64.cu).
+#pragma once
+
+#include "internal.h"
+
+namespace ssilvb {
+
+template <int NB, bool F16, bool INF_T, int SM>
+cudaError_t launch_single_t(const GatherParams &P, const KernelChoice &k, cudaStream_t s) {
+    if (k.mapping == SSILVB_MAP_TILE) {
+        dim3 grid((P.W + 31) / 32, (P.H + 7) / 8);
+        gather_tile_kernel<NB, F16, INF_T, SM><<<grid, 256, 0, s>>>(P);
+    } else {
+        dim3 grid((P.W + 127) / 128, P.H);
+        if (k.minb == 8) gather_class_kernel<NB, F16, INF_T, SM, 8><<<grid, 128, 0, s>>>(P);
+        else gather_class_kernel<NB, F16, INF_T, SM, 10><<<grid, 128, 0, s>>>(P);
+    }
+    return cudaGetLastError();
+}
+
+template <int NB, bool F16, bool INF_T>
+cudaError_t launch_single_s(const GatherParams &P, const KernelChoice &k, cudaStream_t s) {
+    return P.step_mode == 0 ? launch_single_t<NB, F16, INF_T, 0>(P, k, s) : launch_single_t<NB, F16, INF_T, 1>(P, k, s);
+}
+
+template <int NB>
+cudaError_t launch_single_nb(const GatherParams &P, bool f16, bool inf_t, const KernelChoice &k, cudaStream_t s) {
+    if (f16) return inf_t ? launch_single_s<NB, true, true>(P, k, s) : launch_single_s<NB, true, false>(P, k, s);
+    return inf_t ? launch_single_s<NB, false, true>(P, k, s) : launch_single_s<NB, false, false>(P, k, s);
+}
+
+template <int NB, bool F16, bool INF_T, int SM>
+void single_node_t(const GatherParams &P, const KernelChoice &k, const void **fn, dim3 *grid, dim3 *block) {
+    if (k.mapping == SSILVB_MAP_TILE) {
+        *fn = reinterpret_cast<const void *>(gather_tile_kernel<NB, F16, INF_T, SM>);
+        *grid = dim3((P.W + 31) / 32, (P.H + 7) / 8);
+        *block = dim3(256);
+    } else {
+        *fn = k.minb == 8 ? reinterpret_cast<const void *>(gather_class_kernel<NB, F16, INF_T, SM, 8>)
+                          : reinterpret_cast<const void *>(gather_class_kernel<NB, F16, INF_T, SM, 10>);
+        *grid = dim3((P.W + 127) / 128, P.H);
+        *block = dim3(128);
+    }
+}
+
+template <int NB>
+void single_node_nb(const GatherParams &P, bool f16, bool inf_t, const KernelChoice &k, const void **fn, dim3 *grid,
+                    dim3 *block) {
+    const bool s1 = P.step_mode != 0;
+    if (f16) {
+        if (inf_t) s1 ? single_node_t<NB, true, true, 1>(P, k, fn, grid, block) : single_node_t<NB, true, true, 0>(P, k, fn, grid, block);
+        else s1 ? single_node_t<NB, true, false, 1>(P, k, fn, grid, block) : single_node_t<NB, true, false, 0>(P, k, fn, grid, block);
+    } else {
+        if (inf_t) s1 ? single_node_t<NB, false, true, 1>(P, k, fn, grid, block) : single_node_t<NB, false, true, 0>(P, k, fn, grid, block);
+        else s1 ? single_node_t<NB, false, false, 1>(P, k, fn, grid, block) : single_node_t<NB, false, false, 0>(P, k, fn, grid, block);
+    }
+}
+
+template <int NB, bool F16, bool INF_T, int SM>
+cudaError_t launch_batch_t(const BatchHeader *hdr, const FrameDesc *frames, unsigned *queue, const KernelChoice &k,
+                           int grid, cudaStream_t s) {
+    if (k.minb == 8) gather_batch_kernel<NB, F16, INF_T, SM, 8><<<grid, 128, 0, s>>>(hdr, frames, queue);
+    else gather_batch_kernel<NB, F16, INF_T, SM, 10><<<grid, 128, 0, s>>>(hdr, frames, queue);
+    return cudaGetLastError();
+}
+
+template <int NB, bool F16, bool INF_T>
+cudaError_t launch_batch_s(const BatchHeader *hdr, const FrameDesc *frames, unsigned *queue, int step_mode,
+                           const KernelChoice &k, int grid, cudaStream_t s) {
+    return step_mode == 0 ? launch_batch_t<NB, F16, INF_T, 0>(hdr, frames, queue, k, grid, s)
+                          : launch_batch_t<NB, F16, INF_T, 1>(hdr, frames, queue, k, grid, s);
+}
+
+template <int NB>
+cudaError_t launch_batch_nb(const BatchHeader *hdr, const FrameDesc *frames, unsigned *queue, bool f16, bool inf_t,
+                            int step_mode, const KernelChoice &k, int grid, cudaStream_t s) {
+    if (f16)
+        return inf_t ? launch_batch_s<NB, true, true>(hdr, frames, queue, step_mode, k, grid, s)
+                     : launch_batch_s<NB, true, false>(hdr, frames, queue, step_mode, k, grid, s);
+    return inf_t ? launch_batch_s<NB, false, true>(hdr, frames, queue, step_mode, k, grid, s)
+                 : launch_batch_s<NB, false, false>(hdr, frames, queue, step_mode, k, grid, s);
+}
+
+template <int NB, bool F16, bool INF_T>
+int batch_occ_t(int minb) {
+    int n = 0;
+    cudaError_t e = minb == 8
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gather_batch_kernel<NB, F16, INF_T, 0, 8>, 128, 0)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gather_batch_kernel<NB, F16, INF_T, 0, 10>, 128, 0);
+    return e == cudaSuccess ? n : 0;
+}
+
+template <int NB>
+int batch_occ_nb(bool f16, bool inf_t, int minb) {
+    if (f16) return inf_t ? batch_occ_t<NB, true, true>(minb) : batch_occ_t<NB, true, false>(minb);
+    return inf_t ? batch_occ_t<NB, false, true>(minb) : batch_occ_t<NB, false, false>(minb);
+}
+
+}  // namespace ssilvb

@@ -11,25 +11,15 @@
 #include <new>
 #include <string>
 
-#include "gather_kernel.cuh"
-#include "ssilvb.h"
+#include "internal.h"
 
-#define SSILVB_VERSION 10000
+#define SSILVB_VERSION 10100
 
-struct ssilvb_ctx {
-    int device = 0;
-    int num_sms = 0;
-    int *d_status = nullptr;   // device status word (device-side checks and bounded waits)
-    std::string last_error;
-    // staging for ssilvb_gather_host
-    void *stage = nullptr;
-    size_t stage_bytes = 0;
-    ssilvb_tuning tuning = {SSILVB_MAP_AUTO, {0, 0, 0, 0, 0, 0, 0}};
-};
+namespace ssilvb {
 
 namespace {
-
 thread_local std::string g_create_error;
+}  // namespace
 
 ssilvb_status fail(ssilvb_ctx *ctx, ssilvb_status s, const char *fmt, ...) {
     char buf[512];
@@ -46,7 +36,7 @@ ssilvb_status cuda_fail(ssilvb_ctx *ctx, cudaError_t e, const char *what) {
     return fail(ctx, SSILVB_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
 }
 
-bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+static bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
 ssilvb_status validate(ssilvb_ctx *ctx, const ssilvb_gbuffer *g, const ssilvb_camera *c, const ssilvb_params *p,
                        const ssilvb_output *o, bool device_ptrs) {
@@ -196,47 +186,46 @@ void fill_params(ssilvb::GatherParams &P, const ssilvb_gbuffer *g, const ssilvb_
     P.Y4 = (float)(0.25 * std::sqrt(15.0 / M_PI));
 }
 
-template <int NB, bool F16, bool INF_T, int SM>
-cudaError_t launch_t(const ssilvb::GatherParams &P, int mapping, cudaStream_t s) {
-    if (mapping == SSILVB_MAP_TILE) {
-        dim3 grid((P.W + 31) / 32, (P.H + 7) / 8);
-        ssilvb::gather_tile_kernel<NB, F16, INF_T, SM><<<grid, 256, 0, s>>>(P);
-    } else {
-        dim3 grid((P.W + 127) / 128, P.H);
-        ssilvb::gather_class_kernel<NB, F16, INF_T, SM><<<grid, 128, 0, s>>>(P);
-    }
-    return cudaGetLastError();
+cudaError_t launch_single(const GatherParams &P, int nb, bool f16, bool inf_t, const KernelChoice &k, cudaStream_t s) {
+    return nb == 32 ? launch_single_nb32(P, f16, inf_t, k, s) : launch_single_nb64(P, f16, inf_t, k, s);
 }
 
-template <int NB, bool F16, bool INF_T>
-cudaError_t launch_s(const ssilvb::GatherParams &P, int mapping, cudaStream_t s) {
-    return P.step_mode == 0 ? launch_t<NB, F16, INF_T, 0>(P, mapping, s) : launch_t<NB, F16, INF_T, 1>(P, mapping, s);
+void single_kernel_node(const GatherParams &P, int nb, bool f16, bool inf_t, const KernelChoice &k, const void **fn,
+                        dim3 *grid, dim3 *block) {
+    if (nb == 32) single_node_nb32(P, f16, inf_t, k, fn, grid, block);
+    else single_node_nb64(P, f16, inf_t, k, fn, grid, block);
 }
 
-template <int NB>
-cudaError_t launch_nb(const ssilvb::GatherParams &P, bool f16, bool inf_t, int mapping, cudaStream_t s) {
-    if (f16) return inf_t ? launch_s<NB, true, true>(P, mapping, s) : launch_s<NB, true, false>(P, mapping, s);
-    return inf_t ? launch_s<NB, false, true>(P, mapping, s) : launch_s<NB, false, false>(P, mapping, s);
+TuneKey tune_key(const ssilvb_gbuffer *g, const ssilvb_params *p, int batch) {
+    TuneKey k;
+    k.nb = p->sector_count;
+    k.f16 = g->normal_fmt == SSILVB_FMT_F16X4;
+    k.inf_t = std::isinf(p->thickness) ? 1 : 0;
+    const double px = (double)g->width * g->height;
+    k.size_class = (int)std::ceil(std::log2(px > 1.0 ? px : 1.0));
+    k.nd = p->num_slices;
+    k.ns = p->steps_per_side;
+    k.batch = batch;
+    return k;
 }
 
-cudaError_t launch(const ssilvb::GatherParams &P, int nb, bool f16, bool inf_t, int mapping, cudaStream_t s) {
-    if (mapping == SSILVB_MAP_AUTO) mapping = SSILVB_MAP_CLASS;
-    return nb == 32 ? launch_nb<32>(P, f16, inf_t, mapping, s) : launch_nb<64>(P, f16, inf_t, mapping, s);
+KernelChoice resolve_choice(const ssilvb_ctx *ctx, const TuneKey &key) {
+    KernelChoice k;
+    auto it = ctx->tuned.find(key);
+    if (it != ctx->tuned.end()) k = it->second;
+    const ssilvb_tuning &t = ctx->tuning;
+    if (t.mapping != SSILVB_MAP_AUTO) k.mapping = t.mapping;
+    if (t.occupancy) k.minb = t.occupancy;
+    if (t.rows_per_tile) k.rows = t.rows_per_tile;
+    if (t.ctas_per_sm) k.ctas_per_sm = t.ctas_per_sm;
+    if (t.use_graph) k.graph = t.use_graph == 1;
+    if (t.batch_mode) k.batch_mode = t.batch_mode;
+    return k;
 }
 
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard() {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
+}  // namespace ssilvb
 
-}  // namespace
+using namespace ssilvb;
 
 extern "C" {
 
@@ -255,7 +244,9 @@ const char *ssilvb_status_string(ssilvb_status s) {
     return "SSILVB_UNKNOWN_STATUS";
 }
 
-const char *ssilvb_last_error(const ssilvb_ctx *ctx) { return ctx ? ctx->last_error.c_str() : g_create_error.c_str(); }
+const char *ssilvb_last_error(const ssilvb_ctx *ctx) {
+    return ctx ? ctx->last_error.c_str() : ssilvb::g_create_error.c_str();
+}
 
 ssilvb_status ssilvb_create(ssilvb_ctx **out_ctx, int cuda_device) {
     if (!out_ctx) return fail(nullptr, SSILVB_ERR_INVALID_ARG, "out_ctx is NULL");
@@ -272,9 +263,11 @@ ssilvb_status ssilvb_create(ssilvb_ctx **out_ctx, int cuda_device) {
     e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, cuda_device);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         ssilvb_status s = cuda_fail(nullptr, e, "context set-up");
         if (ctx->d_status) cudaFree(ctx->d_status);
+        if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
         delete ctx;
         return e == cudaErrorMemoryAllocation ? SSILVB_ERR_OUT_OF_MEMORY : s;
     }
@@ -288,6 +281,8 @@ ssilvb_status ssilvb_destroy(ssilvb_ctx *ctx) {
     cudaDeviceSynchronize();
     if (ctx->d_status) cudaFree(ctx->d_status);
     if (ctx->stage) cudaFree(ctx->stage);
+    release_batch_slots(ctx);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     delete ctx;
     return SSILVB_OK;
 }
@@ -301,8 +296,9 @@ ssilvb_status ssilvb_gather(ssilvb_ctx *ctx, const ssilvb_gbuffer *gbuffer, cons
     if (s != SSILVB_OK) return s;
     ssilvb::GatherParams P;
     fill_params(P, gbuffer, camera, params, out);
-    cudaError_t e = launch(P, params->sector_count, gbuffer->normal_fmt == SSILVB_FMT_F16X4,
-                           std::isinf(params->thickness), ctx->tuning.mapping, reinterpret_cast<cudaStream_t>(stream));
+    const KernelChoice k = resolve_choice(ctx, tune_key(gbuffer, params, 0));
+    cudaError_t e = launch_single(P, params->sector_count, gbuffer->normal_fmt == SSILVB_FMT_F16X4,
+                                  std::isinf(params->thickness), k, reinterpret_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "gather launch");
     return SSILVB_OK;
 }
@@ -366,8 +362,9 @@ ssilvb_status ssilvb_gather_host(ssilvb_ctx *ctx, const ssilvb_gbuffer *gbuffer,
     ssilvb_output dout = {d_out0, W * 16, d_out1, W * 16, d_masks};
     ssilvb::GatherParams P;
     fill_params(P, &dg_, camera, params, &dout);
-    e = launch(P, params->sector_count, gbuffer->normal_fmt == SSILVB_FMT_F16X4, std::isinf(params->thickness),
-               ctx->tuning.mapping, st);
+    const KernelChoice k = resolve_choice(ctx, tune_key(gbuffer, params, 0));
+    e = launch_single(P, params->sector_count, gbuffer->normal_fmt == SSILVB_FMT_F16X4, std::isinf(params->thickness),
+                      k, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "gather launch");
 
     e = cudaMemcpy2DAsync(out->out0, out->out0_pitch, d_out0, W * 16, W * 16, H, cudaMemcpyDeviceToHost, st);
@@ -386,6 +383,18 @@ ssilvb_status ssilvb_set_tuning(ssilvb_ctx *ctx, const ssilvb_tuning *tuning) {
     if (!tuning) return fail(ctx, SSILVB_ERR_INVALID_ARG, "tuning is NULL");
     if (tuning->mapping < SSILVB_MAP_AUTO || tuning->mapping > SSILVB_MAP_CLASS)
         return fail(ctx, SSILVB_ERR_INVALID_ARG, "unknown mapping %d", tuning->mapping);
+    if (tuning->occupancy != 0 && tuning->occupancy != 8 && tuning->occupancy != 10)
+        return fail(ctx, SSILVB_ERR_INVALID_ARG, "occupancy must be 0, 8 or 10");
+    if (tuning->rows_per_tile < 0 || tuning->rows_per_tile > 8)
+        return fail(ctx, SSILVB_ERR_INVALID_ARG, "rows_per_tile must be 0..8");
+    if (tuning->ctas_per_sm < 0 || tuning->ctas_per_sm > 16)
+        return fail(ctx, SSILVB_ERR_INVALID_ARG, "ctas_per_sm must be 0..16");
+    if (tuning->use_graph < 0 || tuning->use_graph > 2)
+        return fail(ctx, SSILVB_ERR_INVALID_ARG, "use_graph must be 0, 1 or 2");
+    if (tuning->batch_mode < 0 || tuning->batch_mode > 2)
+        return fail(ctx, SSILVB_ERR_INVALID_ARG, "batch_mode must be 0, 1 or 2");
+    for (int i = 0; i < 2; ++i)
+        if (tuning->reserved[i]) return fail(ctx, SSILVB_ERR_INVALID_ARG, "reserved tuning fields must be zero");
     ctx->tuning = *tuning;
     return SSILVB_OK;
 }
