@@ -204,6 +204,25 @@ ssilvb_status ssilvb_gather_batch(ssilvb_ctx *ctx, const ssilvb_frame *frames, i
 ssilvb_status ssilvb_autotune(ssilvb_ctx *ctx, const ssilvb_frame *frames, int n_frames, struct CUstream_st *stream,
                               ssilvb_tuning *chosen);
 
+/* The batch gather of ssilvb_gather_batch (persistent-kernel form) for callers that cannot
+ * allocate device memory when they call it: an engine that reserves its whole GPU budget up
+ * front and forbids driver allocations in its frame loop, code running while a global-mode
+ * stream capture is active (cudaMalloc is illegal there), or a plug-in whose host application
+ * owns all device memory; cudaMalloc also synchronises the device, which a real-time loop
+ * cannot afford.  The paper has no counterpart: this is an interface choice only.
+ * No context: it runs on the CURRENT device, and its scratch (the work list and the tile-queue
+ * counter) lives in a fixed array inside the library, about 44 KB that every GPU loading the
+ * library holds until the process exits.  The call allocates nothing (no cudaMalloc,
+ * cudaFree, graph or event); the caller still passes all inputs and outputs, with the same
+ * rules as ssilvb_gather_batch.  At most 16 frames (INVALID_ARG beyond, with the limit in the
+ * message).  The first call on a device looks up the array's device address (and loads the
+ * kernels if CUDA loads modules lazily), so make it before any stream capture.  Every call
+ * shares the array and overwrites the previous call's work list: calls whose work overlaps on
+ * the GPU race and give wrong results, so issue them on one stream or order them.
+ * Asynchronous on stream; the host frame array is read during the call only.  Error detail:
+ * ssilvb_last_error(NULL) in the calling thread. */
+ssilvb_status ssilvb_gather_batch_noalloc(const ssilvb_frame *frames, int n_frames, struct CUstream_st *stream);
+
 /* Set the context's launch choices for later calls (copied).  INVALID_ARG on an unknown value. */
 ssilvb_status ssilvb_set_tuning(ssilvb_ctx *ctx, const ssilvb_tuning *tuning);
 

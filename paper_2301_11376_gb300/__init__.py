@@ -37,7 +37,7 @@ def _sources():
     return [os.path.join(_CSRC, f) for f in sorted(os.listdir(_CSRC))] + [os.path.join(INCLUDE, "ssilvb.h")]
 
 
-UNITS = ["ssilvb.cu", "batch.cu", "launch_nb32.cu", "launch_nb64.cu"]
+UNITS = ["ssilvb.cu", "batch.cu", "launch_nb32.cu", "launch_nb64.cu", "noalloc.cu"]
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
@@ -140,6 +140,8 @@ def load():
     lib.ssilvb_gather_batch.restype = ctypes.c_int
     lib.ssilvb_autotune.argtypes = [vp, ctypes.POINTER(Frame), ctypes.c_int, vp, ctypes.POINTER(Tuning)]
     lib.ssilvb_autotune.restype = ctypes.c_int
+    lib.ssilvb_gather_batch_noalloc.argtypes = [ctypes.POINTER(Frame), ctypes.c_int, vp]
+    lib.ssilvb_gather_batch_noalloc.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -326,6 +328,19 @@ class Context:
 
     def synchronize(self, stream=None):
         self._check(self.lib.ssilvb_synchronize(self.handle, ctypes.c_void_p(stream.cuda_stream if stream else None)))
+
+
+def gather_batch_noalloc(frames, stream=None):
+    """ssilvb_gather_batch_noalloc: the batch gather on the current device without any device
+    allocation (scratch in a fixed array inside the library; at most 16 frames).  For callers
+    that cannot allocate GPU memory when they run the gather."""
+    import torch
+    lib = load()
+    arr = (Frame * len(frames))(*frames)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    rc = lib.ssilvb_gather_batch_noalloc(arr, len(frames), ctypes.c_void_p(s.cuda_stream))
+    if rc != SSILVB_OK:
+        raise SsilvbError(rc, lib.ssilvb_last_error(None).decode())
 
 
 def alloc_outputs(H: int, W: int, params, device="cuda", masks: bool = False):
