@@ -1,0 +1,273 @@
+"""Continuous-batching server for the visibility-bitmask gather.
+
+Requests name a G-buffer that stays resident on the device and carry their own parameters
+(slices, steps, sector count ...).  The loop admits arrived requests into the next batch as
+soon as an in-flight slot and output memory are free, launches each batch with
+``ssilvb_gather_batch`` on one of several streams (so batches overlap on the GPU), and
+records each request's completion on the device clock.  Output memory comes from one
+device arena with a first-fit free list; a request waits while its outputs do not fit, and
+arrivals beyond a bounded queue are shed and counted.
+
+``PlainServer`` is the naive baseline: one request at a time, one ``ssilvb_gather`` launch
+and one host synchronisation per request, same queue bound.
+"""
+from __future__ import annotations
+
+import bisect
+import collections
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival: float          # seconds after the start of the run
+    key: object             # resident G-buffer key
+    params: object          # scenegen.Params-like (num_slices, steps_per_side, sector_count, ...)
+    noise: np.ndarray | None = None
+    sh: np.ndarray | None = None
+
+
+@dataclass
+class Stats:
+    served: int = 0
+    dropped: int = 0
+    latencies_ms: list = field(default_factory=list)
+    wall_s: float = 0.0
+    batches: int = 0
+    max_inflight_seen: int = 0
+    samples: int = 0
+
+    def summary(self):
+        lat = np.asarray(self.latencies_ms) if self.latencies_ms else np.zeros(1)
+        return {"served": self.served, "dropped": self.dropped,
+                "frames_per_s": self.served / self.wall_s if self.wall_s > 0 else 0.0,
+                "gsamples_per_s": self.samples / self.wall_s / 1e9 if self.wall_s > 0 else 0.0,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "mean_ms": float(lat.mean()), "batches": self.batches,
+                "max_batches_in_flight": self.max_inflight_seen, "wall_s": self.wall_s}
+
+
+class ResidentPool:
+    """G-buffers resident on the device, by key: (depth, normal, radiance, camera)."""
+
+    def __init__(self, device="cuda"):
+        self.device = device
+        self.items = {}
+
+    def add(self, key, gbuf):
+        import torch
+        d = torch.from_numpy(np.ascontiguousarray(gbuf.depth)).to(self.device)
+        n = torch.from_numpy(np.ascontiguousarray(gbuf.normal)).to(self.device)
+        r = torch.from_numpy(np.ascontiguousarray(gbuf.radiance)).to(self.device)
+        self.items[key] = (d, n, r, gbuf.camera)
+
+    def shape(self, key):
+        return tuple(self.items[key][0].shape)
+
+
+class OutputArena:
+    """First-fit allocator over one device buffer (256-byte aligned blocks)."""
+
+    ALIGN = 256
+
+    def __init__(self, nbytes, device="cuda"):
+        import torch
+        self.buf = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        self.size = nbytes
+        self.free = [(0, nbytes)]  # sorted (offset, size)
+
+    def alloc(self, nbytes):
+        nbytes = (nbytes + self.ALIGN - 1) // self.ALIGN * self.ALIGN
+        for i, (off, sz) in enumerate(self.free):
+            if sz >= nbytes:
+                if sz == nbytes:
+                    self.free.pop(i)
+                else:
+                    self.free[i] = (off + nbytes, sz - nbytes)
+                return off, nbytes
+        return None
+
+    def release(self, off, nbytes):
+        i = bisect.bisect(self.free, (off, 0))
+        self.free.insert(i, (off, nbytes))
+        # merge neighbours
+        merged = []
+        for o, s in self.free:
+            if merged and merged[-1][0] + merged[-1][1] == o:
+                merged[-1] = (merged[-1][0], merged[-1][1] + s)
+            else:
+                merged.append((o, s))
+        self.free = merged
+
+    def view(self, off, H, W):
+        import torch
+        return self.buf[off:off + H * W * 16].view(torch.float32).view(H, W, 4)
+
+
+def _out_bytes(H, W, prm):
+    return H * W * 16 * (2 if prm.ambient_cones > 0 else 1)
+
+
+class Server:
+    """Continuous batching: batches of arrived requests, several in flight on separate streams."""
+
+    def __init__(self, ctx, pool, arena_bytes=1 << 31, max_inflight=4, max_batch=16, max_queue=256, streams=3):
+        import torch
+        self.ctx, self.pool = ctx, pool
+        self.arena = OutputArena(arena_bytes, pool.device)
+        self.max_inflight, self.max_batch, self.max_queue = max_inflight, max_batch, max_queue
+        self.streams = [torch.cuda.Stream() for _ in range(streams)]
+
+    def run(self, requests, on_done=None, timeout_s=120.0):
+        import torch
+        st = Stats()
+        reqs = sorted(requests, key=lambda r: r.arrival)
+        pending = collections.deque()
+        inflight = collections.deque()  # (event, [(req, off, nbytes, out0, out1)])
+        base = torch.cuda.Event(enable_timing=True)
+        base.record()
+        base.synchronize()
+        t0 = time.perf_counter()
+        i, si = 0, 0
+        last_done = 0.0
+        while i < len(reqs) or pending or inflight:
+            now = time.perf_counter() - t0
+            if now > timeout_s:
+                raise RuntimeError("serving run exceeded its time limit")
+            while i < len(reqs) and reqs[i].arrival <= now:
+                if len(pending) < self.max_queue:
+                    pending.append(reqs[i])
+                else:
+                    st.dropped += 1
+                i += 1
+            # completions, in launch order
+            while inflight and inflight[0][0].query():
+                ev, items = inflight.popleft()
+                t_done = base.elapsed_time(ev) / 1e3
+                last_done = max(last_done, t_done)
+                for req, off, nb_, o0, o1 in items:
+                    st.latencies_ms.append((t_done - req.arrival) * 1e3)
+                    st.served += 1
+                    if on_done is not None:
+                        on_done(req, o0, o1)
+                    self.arena.release(off, nb_)
+            # admit and launch the next batch
+            if pending and len(inflight) < self.max_inflight:
+                head_nb = pending[0].params.sector_count
+                batch, keep, frames = [], None, []
+                skipped = collections.deque()
+                while pending and len(batch) < self.max_batch:
+                    req = pending.popleft()
+                    if req.params.sector_count != head_nb:
+                        skipped.append(req)
+                        continue
+                    H, W = self.pool.shape(req.key)
+                    nbytes = _out_bytes(H, W, req.params)
+                    got = self.arena.alloc(nbytes)
+                    if got is None:  # wait for memory: keep the request at its place in the queue
+                        skipped.append(req)
+                        break
+                    off, nb_ = got
+                    o0 = self.arena.view(off, H, W)
+                    o1 = self.arena.view(off + H * W * 16, H, W) if req.params.ambient_cones > 0 else None
+                    d, n, r, cam = self.pool.items[req.key]
+                    f, keep = self.ctx.frame(d, n, r, cam, req.params, o0, o1, None, noise=req.noise, sh=req.sh,
+                                             keep=keep)
+                    frames.append(f)
+                    batch.append((req, off, nb_, o0, o1))
+                    st.samples += H * W * 2 * req.params.num_slices * req.params.steps_per_side
+                while skipped:
+                    pending.appendleft(skipped.pop())
+                if batch:
+                    s = self.streams[si % len(self.streams)]
+                    si += 1
+                    self.ctx.gather_batch(frames, stream=s)
+                    ev = torch.cuda.Event(enable_timing=True)
+                    ev.record(s)
+                    inflight.append((ev, batch))
+                    st.batches += 1
+                    st.max_inflight_seen = max(st.max_inflight_seen, len(inflight))
+                    continue
+            time.sleep(0.0001)
+        st.wall_s = max(last_done, 1e-9) - (reqs[0].arrival if reqs else 0.0)
+        return st
+
+
+class PlainServer:
+    """Naive baseline: one launch and one host synchronisation per request, in arrival order."""
+
+    def __init__(self, ctx, pool, max_queue=256):
+        self.ctx, self.pool, self.max_queue = ctx, pool, max_queue
+        self.outs = {}
+
+    def _outputs(self, key, prm):
+        import torch
+        k = (key, prm.ambient_cones > 0)
+        if k not in self.outs:
+            H, W = self.pool.shape(key)
+            o0 = torch.empty((H, W, 4), dtype=torch.float32, device=self.pool.device)
+            o1 = torch.empty((H, W, 4), dtype=torch.float32, device=self.pool.device) if prm.ambient_cones else None
+            self.outs[k] = (o0, o1)
+        return self.outs[k]
+
+    def run(self, requests, on_done=None, timeout_s=120.0):
+        import torch
+        st = Stats()
+        reqs = sorted(requests, key=lambda r: r.arrival)
+        stream = torch.cuda.Stream()
+        t0 = time.perf_counter()
+        last_done = 0.0
+        waiting = collections.deque()
+        i = 0
+        while i < len(reqs) or waiting:
+            now = time.perf_counter() - t0
+            if now > timeout_s:
+                raise RuntimeError("serving run exceeded its time limit")
+            while i < len(reqs) and reqs[i].arrival <= now:
+                if len(waiting) < self.max_queue:
+                    waiting.append(reqs[i])
+                else:
+                    st.dropped += 1
+                i += 1
+            if not waiting:
+                time.sleep(0.0001)
+                continue
+            req = waiting.popleft()
+            d, n, r, cam = self.pool.items[req.key]
+            o0, o1 = self._outputs(req.key, req.params)
+            self.ctx.gather(d, n, r, cam, req.params, o0, o1, None, noise=req.noise, sh=req.sh, stream=stream)
+            stream.synchronize()
+            t_done = time.perf_counter() - t0
+            last_done = t_done
+            st.latencies_ms.append((t_done - req.arrival) * 1e3)
+            st.served += 1
+            H, W = self.pool.shape(req.key)
+            st.samples += H * W * 2 * req.params.num_slices * req.params.steps_per_side
+            if on_done is not None:
+                on_done(req, o0, o1)
+        st.wall_s = max(last_done, 1e-9) - (reqs[0].arrival if reqs else 0.0)
+        st.batches = st.served
+        return st
+
+
+def poisson_requests(seed, n, mean_gap_s, keys, sizes_of, nd_range=(1, 8), nb_choices=(32, 64),
+                     ns_choices=(8, 16, 32), radius=2.0, thickness=0.5):
+    """A seeded Poisson arrival stream over resident G-buffer keys with per-request parameters."""
+    import scenegen
+    u = scenegen.uniform(seed, 6 * n)
+    t = 0.0
+    out = []
+    noise = scenegen.ign_table()
+    for k in range(n):
+        t += -mean_gap_s * np.log(max(1.0 - u[6 * k], 1e-12))
+        key = keys[min(int(u[6 * k + 1] * len(keys)), len(keys) - 1)]
+        nd = nd_range[0] + min(int(u[6 * k + 2] * (nd_range[1] - nd_range[0] + 1)), nd_range[1] - nd_range[0])
+        nb = nb_choices[min(int(u[6 * k + 3] * len(nb_choices)), len(nb_choices) - 1)]
+        ns = ns_choices[min(int(u[6 * k + 4] * len(ns_choices)), len(ns_choices) - 1)]
+        prm = scenegen.Params(num_slices=nd, steps_per_side=ns, radius=radius, thickness=thickness, sector_count=nb)
+        out.append(Request(k, t, key, prm, noise, None))
+    return out
