@@ -72,9 +72,13 @@ typedef struct {
     const void *normal;           /* view-space unit normal, xyz used */
     size_t normal_pitch;
     int normal_fmt;               /* ssilvb_format */
-    const void *radiance;         /* direct radiance, rgb used */
+    const void *radiance;         /* light buffer, rgb used: direct radiance (plus the previous
+                                     frame's injected bounce under multi-bounce) */
     size_t radiance_pitch;
     int radiance_fmt;             /* ssilvb_format */
+    const void *direct;           /* optional, multi-bounce only: this frame's direct radiance, in
+                                     the radiance format; NULL = the radiance plane is direct light */
+    size_t direct_pitch;
 } ssilvb_gbuffer;
 
 /* Pinhole intrinsics in pixels (fx, fy > 0) and the row-major view->world
@@ -102,6 +106,7 @@ typedef struct {
     const float *sh_rgb;   /* HOST, 9 x 3 real SH radiance coefficients [m][rgb] of the ambient
                               environment (order Y00, Y1-1, Y10, Y11, Y2-2, Y2-1, Y20, Y21, Y22);
                               required iff ambient_cones > 0 */
+    float bounce_gain;     /* multi-bounce (Section 4.3): g >= 0, finite; used only with out->light_out */
 } ssilvb_params;
 
 /* Outputs, device pointers.  out0 (required): float4 per pixel = (GI.r, GI.g, GI.b, AO),
@@ -109,13 +114,20 @@ typedef struct {
  * out1 (required iff ambient_cones > 0): float4 = (ambient.r, .g, .b, 0).
  * Pitches in bytes, multiples of 16; bases 16-byte aligned.
  * masks (optional, NULL = not written): the final slice bitmasks, dense
- * [num_slices][height][width] of uint32 (N_b = 32) or uint64 (N_b = 64), 8-byte aligned. */
+ * [num_slices][height][width] of uint32 (N_b = 32) or uint64 (N_b = 64), 8-byte aligned.
+ * light_out (optional, NULL = not written): the light buffer for the next frame of the
+ * multi-bounce scheme of Section 4.3, direct + bounce_gain * GI per channel (4th = 0), where
+ * direct is gbuffer->direct (or the radiance plane when that is NULL), in the radiance plane's
+ * format and pitch rules; it must not be the radiance or direct plane (the caller alternates
+ * two light buffers between frames).  A gain below 1 keeps the feedback bounded. */
 typedef struct {
     float *out0;
     size_t out0_pitch;
     float *out1;
     size_t out1_pitch;
     void *masks;
+    void *light_out;
+    size_t light_out_pitch;
 } ssilvb_output;
 
 /* Launch choices.  None of them changes any result: every choice gives bit-identical output.

@@ -76,7 +76,8 @@ class Gbuffer(ctypes.Structure):
     _fields_ = [("width", ctypes.c_int), ("height", ctypes.c_int),
                 ("depth", ctypes.c_void_p), ("depth_pitch", ctypes.c_size_t),
                 ("normal", ctypes.c_void_p), ("normal_pitch", ctypes.c_size_t), ("normal_fmt", ctypes.c_int),
-                ("radiance", ctypes.c_void_p), ("radiance_pitch", ctypes.c_size_t), ("radiance_fmt", ctypes.c_int)]
+                ("radiance", ctypes.c_void_p), ("radiance_pitch", ctypes.c_size_t), ("radiance_fmt", ctypes.c_int),
+                ("direct", ctypes.c_void_p), ("direct_pitch", ctypes.c_size_t)]
 
 
 class CameraC(ctypes.Structure):
@@ -88,12 +89,14 @@ class ParamsC(ctypes.Structure):
     _fields_ = [("num_slices", ctypes.c_int), ("steps_per_side", ctypes.c_int), ("radius", ctypes.c_float),
                 ("thickness", ctypes.c_float), ("thickness_slope", ctypes.c_float), ("sector_count", ctypes.c_int),
                 ("hit_rule", ctypes.c_int), ("step_mode", ctypes.c_int), ("ambient_cones", ctypes.c_int),
-                ("compute_gi", ctypes.c_int), ("noise_table", ctypes.c_void_p), ("sh_rgb", ctypes.c_void_p)]
+                ("compute_gi", ctypes.c_int), ("noise_table", ctypes.c_void_p), ("sh_rgb", ctypes.c_void_p),
+                ("bounce_gain", ctypes.c_float)]
 
 
 class Output(ctypes.Structure):
     _fields_ = [("out0", ctypes.c_void_p), ("out0_pitch", ctypes.c_size_t), ("out1", ctypes.c_void_p),
-                ("out1_pitch", ctypes.c_size_t), ("masks", ctypes.c_void_p)]
+                ("out1_pitch", ctypes.c_size_t), ("masks", ctypes.c_void_p), ("light_out", ctypes.c_void_p),
+                ("light_out_pitch", ctypes.c_size_t)]
 
 
 class Frame(ctypes.Structure):
@@ -200,6 +203,7 @@ def _params_c(p, keep: _HostArrays, noise=None, sh=None) -> ParamsC:
     c.compute_gi = 1 if getattr(p, "gi", True) else 0
     c.noise_table = keep.ptr(noise, 32)
     c.sh_rgb = keep.ptr(sh, 27) if (sh is not None and p.ambient_cones > 0) else None
+    c.bounce_gain = float(getattr(p, "bounce_gain", 0.0))
     return c
 
 
@@ -249,17 +253,20 @@ class Context:
             raise SsilvbError(rc, self.lib.ssilvb_last_error(self.handle).decode())
 
     def gather(self, depth, normal, radiance, camera, params, out0, out1=None, masks=None, noise=None, sh=None,
-               stream=None):
+               stream=None, light_out=None, direct=None):
         """ssilvb_gather on device tensors: depth [H,W] f32, normal/radiance [H,W,4] f32|f16,
         out0 [H,W,4] f32, out1 [H,W,4] f32 (ambient), masks [N_d,H,W] int32|int64 or None."""
         import torch
         H, W = depth.shape
         g = Gbuffer(W, H, depth.data_ptr(), _pitch(depth, 1), normal.data_ptr(), _pitch(normal, 4), _fmt(normal),
-                    radiance.data_ptr(), _pitch(radiance, 4), _fmt(radiance))
+                    radiance.data_ptr(), _pitch(radiance, 4), _fmt(radiance),
+                    direct.data_ptr() if direct is not None else None, _pitch(direct, 4) if direct is not None else 0)
         keep = _HostArrays()
         pc = _params_c(params, keep, noise, sh)
         o = Output(out0.data_ptr(), _pitch(out0, 4), out1.data_ptr() if out1 is not None else None,
-                   _pitch(out1, 4) if out1 is not None else 0, masks.data_ptr() if masks is not None else None)
+                   _pitch(out1, 4) if out1 is not None else 0, masks.data_ptr() if masks is not None else None,
+                   light_out.data_ptr() if light_out is not None else None,
+                   _pitch(light_out, 4) if light_out is not None else 0)
         if stream is None:
             stream = torch.cuda.current_stream(depth.device if depth.is_cuda else None)
         s = stream

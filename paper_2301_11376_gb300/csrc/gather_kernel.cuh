@@ -40,6 +40,11 @@ struct GatherParams {
     float *out0;
     float *out1;
     void *masks;
+    char *light_out;       // multi-bounce light buffer for the next frame (or null)
+    size_t light_pitch;    // bytes
+    const char *direct;    // this frame's direct light for the bounce epilogue
+    size_t direct_pitch;   // bytes
+    float gain;            // bounce gain
     size_t depth_pitch;    // elements (floats)
     size_t normal_pitch;   // bytes
     size_t radiance_pitch; // bytes
@@ -154,6 +159,23 @@ __device__ __forceinline__ float3 load_xyz(const char *base, size_t pitch, int x
 
 // 0 < z < +INF (NaN and negative values fail): positive finite binary32 bit patterns are 1 .. 0x7f7fffff.
 __device__ __forceinline__ bool is_geometry(float z) { return __float_as_uint(z) - 1u < 0x7f7fffffu; }
+
+// Multi-bounce epilogue (Section 4.3): the next frame's light = direct + gain * GI.
+template <bool F16>
+__device__ __forceinline__ void write_light(const GatherParams &P, int x, int y, float gr, float gg, float gb) {
+    const float3 c = load_xyz<F16>(P.direct, P.direct_pitch, x, y);
+    const float r = fmaf(P.gain, gr, c.x), g = fmaf(P.gain, gg, c.y), b = fmaf(P.gain, gb, c.z);
+    char *row = P.light_out + (size_t)y * P.light_pitch;
+    if (F16) {
+        const __half2 h0 = __floats2half2_rn(r, g), h1 = __floats2half2_rn(b, 0.0f);
+        uint2 v;
+        v.x = *reinterpret_cast<const uint32_t *>(&h0);
+        v.y = *reinterpret_cast<const uint32_t *>(&h1);
+        reinterpret_cast<uint2 *>(row)[x] = v;
+    } else {
+        reinterpret_cast<float4 *>(row)[x] = make_float4(r, g, b, 0.0f);
+    }
+}
 
 // Which pixel step j of a side reads (nearest pixel, ties to even, through the 1.5*2^23
 // add), whether it is on screen and not the centre pixel, and its depth (loaded now so
@@ -287,6 +309,7 @@ __device__ __forceinline__ void gather_pixel(const GatherParams &P, int x, int y
         if (P.na > 0) *(reinterpret_cast<float4 *>(P.out1 + (size_t)y * P.out1_pitch) + x) = make_float4(0, 0, 0, 0);
         if (P.masks)
             for (int i = 0; i < P.nd; ++i) reinterpret_cast<M *>(P.masks)[((size_t)i * P.H + y) * P.W + x] = 0;
+        if (P.light_out) write_light<F16>(P, x, y, 0.0f, 0.0f, 0.0f);
         return;
     }
 
@@ -395,7 +418,9 @@ __device__ __forceinline__ void gather_pixel(const GatherParams &P, int x, int y
         }
         if (P.masks) reinterpret_cast<M *>(P.masks)[((size_t)i * P.H + y) * P.W + x] = b;
     }
-    *o0 = make_float4(GIr * P.inv_nd, GIg * P.inv_nd, GIb * P.inv_nd, AO * P.inv_nd);
+    const float gr = GIr * P.inv_nd, gg = GIg * P.inv_nd, gb = GIb * P.inv_nd;
+    *o0 = make_float4(gr, gg, gb, AO * P.inv_nd);
+    if (P.light_out) write_light<F16>(P, x, y, gr, gg, gb);
     if (P.na > 0)
         *(reinterpret_cast<float4 *>(P.out1 + (size_t)y * P.out1_pitch) + x) =
             make_float4(AMr * P.inv_nd, AMg * P.inv_nd, AMb * P.inv_nd, 0.0f);

@@ -98,8 +98,19 @@ ssilvb_status validate(ssilvb_ctx *ctx, const ssilvb_gbuffer *g, const ssilvb_ca
     if (na > 0 && (!o->out1 || o->out1_pitch < W * 16 || o->out1_pitch % 16 || !aligned(o->out1, 16)))
         return fail(ctx, SSILVB_ERR_INVALID_ARG, "out1 (16-byte aligned, pitch >= 16*width) required with ambient cones");
     if (o->masks && !aligned(o->masks, 8)) return fail(ctx, SSILVB_ERR_INVALID_ARG, "masks must be 8-byte aligned");
+    if (o->light_out) {
+        if (!aligned(o->light_out, 16) || o->light_out_pitch < W * px || o->light_out_pitch % px)
+            return fail(ctx, SSILVB_ERR_INVALID_ARG, "light_out: 16-byte aligned, pitch a multiple of %zu >= width", px);
+        if (o->light_out == g->radiance || (g->direct && o->light_out == g->direct))
+            return fail(ctx, SSILVB_ERR_INVALID_ARG, "light_out must not be an input plane (use two buffers)");
+        if (g->direct && (!aligned(g->direct, 16) || g->direct_pitch < W * px || g->direct_pitch % px))
+            return fail(ctx, SSILVB_ERR_INVALID_ARG, "direct: 16-byte aligned, pitch a multiple of %zu >= width", px);
+        if (!(p->bounce_gain >= 0.0f) || !std::isfinite(p->bounce_gain))
+            return fail(ctx, SSILVB_ERR_INVALID_ARG, "bounce_gain must be finite and >= 0");
+    }
     if (device_ptrs) {
-        const void *ptrs[] = {g->depth, g->normal, g->radiance, o->out0, na > 0 ? o->out1 : nullptr, o->masks};
+        const void *ptrs[] = {g->depth, g->normal, g->radiance, o->out0, na > 0 ? o->out1 : nullptr, o->masks,
+                              o->light_out, o->light_out ? g->direct : nullptr};
         for (const void *q : ptrs) {
             if (!q) continue;
             cudaPointerAttributes a;
@@ -129,6 +140,12 @@ void fill_params(ssilvb::GatherParams &P, const ssilvb_gbuffer *g, const ssilvb_
     P.out0 = o->out0;
     P.out1 = p->ambient_cones > 0 ? o->out1 : nullptr;
     P.masks = o->masks;
+    P.light_out = static_cast<char *>(o->light_out);
+    P.light_pitch = o->light_out ? o->light_out_pitch : 0;
+    P.gain = o->light_out ? p->bounce_gain : 0.0f;
+    const bool own_direct = o->light_out && g->direct;
+    P.direct = own_direct ? static_cast<const char *>(g->direct) : static_cast<const char *>(g->radiance);
+    P.direct_pitch = own_direct ? g->direct_pitch : g->radiance_pitch;
     P.depth_pitch = g->depth_pitch / 4;
     P.normal_pitch = g->normal_pitch;
     P.radiance_pitch = g->radiance_pitch;
@@ -318,7 +335,9 @@ ssilvb_status ssilvb_gather_host(ssilvb_ctx *ctx, const ssilvb_gbuffer *gbuffer,
     const size_t mask_bytes = out->masks ? (size_t)params->num_slices * W * H * (params->sector_count / 8) : 0;
     auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
     const size_t b_depth = up(W * H * 4), b_px = up(W * H * px), b_out = up(W * H * 16);
-    const size_t need = b_depth + 2 * b_px + b_out + (na > 0 ? b_out : 0) + up(mask_bytes);
+    const size_t b_light = out->light_out ? up(W * H * px) : 0;
+    const size_t b_direct = (out->light_out && gbuffer->direct) ? up(W * H * px) : 0;
+    const size_t need = b_depth + 2 * b_px + b_out + (na > 0 ? b_out : 0) + up(mask_bytes) + b_light + b_direct;
     if (need > ctx->stage_bytes) {
         if (ctx->stage) {
             cudaError_t e = cudaStreamSynchronize(st);
@@ -341,6 +360,11 @@ ssilvb_status ssilvb_gather_host(ssilvb_ctx *ctx, const ssilvb_gbuffer *gbuffer,
     float *d_out0 = reinterpret_cast<float *>(d_rad + b_px);
     float *d_out1 = na > 0 ? reinterpret_cast<float *>(reinterpret_cast<char *>(d_out0) + b_out) : nullptr;
     void *d_masks = out->masks ? reinterpret_cast<char *>(d_out0) + b_out + (na > 0 ? b_out : 0) : nullptr;
+    void *d_light = out->light_out ? reinterpret_cast<char *>(d_out0) + b_out + (na > 0 ? b_out : 0) + up(mask_bytes)
+                                   : nullptr;
+    void *d_direct = b_direct ? reinterpret_cast<char *>(d_out0) + b_out + (na > 0 ? b_out : 0) + up(mask_bytes) +
+                                    b_light
+                              : nullptr;
 
     cudaError_t e = cudaMemcpy2DAsync(d_depth, W * 4, gbuffer->depth, gbuffer->depth_pitch, W * 4, H,
                                       cudaMemcpyHostToDevice, st);
@@ -350,16 +374,21 @@ ssilvb_status ssilvb_gather_host(ssilvb_ctx *ctx, const ssilvb_gbuffer *gbuffer,
     if (e == cudaSuccess)
         e = cudaMemcpy2DAsync(d_rad, W * px, gbuffer->radiance, gbuffer->radiance_pitch, W * px, H,
                               cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && d_direct)
+        e = cudaMemcpy2DAsync(d_direct, W * px, gbuffer->direct, gbuffer->direct_pitch, W * px, H,
+                              cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "host-to-device copy");
 
     ssilvb_gbuffer dg_ = *gbuffer;
+    dg_.direct = d_direct;
+    dg_.direct_pitch = d_direct ? W * px : 0;
     dg_.depth = d_depth;
     dg_.depth_pitch = W * 4;
     dg_.normal = d_normal;
     dg_.normal_pitch = W * px;
     dg_.radiance = d_rad;
     dg_.radiance_pitch = W * px;
-    ssilvb_output dout = {d_out0, W * 16, d_out1, W * 16, d_masks};
+    ssilvb_output dout = {d_out0, W * 16, d_out1, W * 16, d_masks, d_light, W * px};
     ssilvb::GatherParams P;
     fill_params(P, &dg_, camera, params, &dout);
     const KernelChoice k = resolve_choice(ctx, tune_key(gbuffer, params, 0));
@@ -372,6 +401,9 @@ ssilvb_status ssilvb_gather_host(ssilvb_ctx *ctx, const ssilvb_gbuffer *gbuffer,
         e = cudaMemcpy2DAsync(out->out1, out->out1_pitch, d_out1, W * 16, W * 16, H, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess && out->masks)
         e = cudaMemcpyAsync(out->masks, d_masks, mask_bytes, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && out->light_out)
+        e = cudaMemcpy2DAsync(out->light_out, out->light_out_pitch, d_light, W * px, W * px, H, cudaMemcpyDeviceToHost,
+                              st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "device-to-host copy");
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "gather execution");

@@ -164,6 +164,7 @@ class Params:
     ambient_cones: int = 0
     step_mode: int = 0  # 0 = constant steps, 1 = exponential (quadratic) steps
     gi: bool = True
+    bounce_gain: float = 0.0
 
 
 @dataclass

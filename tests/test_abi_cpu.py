@@ -45,10 +45,10 @@ def test_status_strings(lib):
 
 def test_struct_layouts_match_header():
     # sizes of the ctypes mirrors on this ABI (LP64): checked against the C declarations
-    assert ctypes.sizeof(ssilvb.Gbuffer) == 8 + 8 * 2 + (8 + 8 + 8) * 2
+    assert ctypes.sizeof(ssilvb.Gbuffer) == 8 + 8 * 2 + (8 + 8 + 8) * 2 + 16
     assert ctypes.sizeof(ssilvb.CameraC) == 13 * 4
-    assert ctypes.sizeof(ssilvb.ParamsC) == 4 * 10 + 16
-    assert ctypes.sizeof(ssilvb.Output) == 5 * 8
+    assert ctypes.sizeof(ssilvb.ParamsC) == 4 * 10 + 16 + 8
+    assert ctypes.sizeof(ssilvb.Output) == 7 * 8
 
 
 def test_null_arguments_rejected_without_gpu(lib):
