@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ssilvb", choices=["ssilvb", "reference"])
-    ap.add_argument("--workload", default="4k", choices=["4k", "1080p", "256", "batch", "serve"])
+    ap.add_argument("--workload", default="4k", choices=["4k", "1080p", "256", "batch", "serve", "trends"])
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--nb", type=int, default=32)
     ap.add_argument("--no-e2e", action="store_true")
@@ -298,6 +298,67 @@ def run_batch_bench(args, world, rank, local):
     print(json.dumps(out))
 
 
+def run_trend_sweep(args, world, rank, local):
+    """Sweeps shaped like the paper's Table 1 (AO only, 1080p, one slice per pixel, N_b 32:
+    radius/steps pairs, bitmask t = 0.5 m vs infinite thickness = horizon mode; plus N_b 128)
+    and Table 2 (indirect diffuse, t = 0.2 m, constant vs quadratic steps, half resolution).
+    Reproduces trends only; the paper's numbers are from an RTX 2080 on another scene."""
+    import torch
+
+    import paper_2301_11376_gb300 as ssilvb
+    ssilvb.build()
+    if rank != 0:
+        return
+    dev = torch.device("cuda", local)
+    ctx = ssilvb.Context(local)
+    noise = scenegen.ign_table()
+    full = scenegen.render(2, 1920, 1080, 64, 16)
+    half = scenegen.render(2, 960, 540, 64, 16)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def dev_gb(g):
+        return tuple(torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (g.depth, g.normal, g.radiance))
+
+    gbs = {"full": (full, dev_gb(full)), "half": (half, dev_gb(half))}
+
+    def time_one(res, prm, reps=12):
+        g, (d, n, r) = gbs[res]
+        H, W = g.depth.shape
+        o0, _, _ = ssilvb.alloc_outputs(H, W, prm, dev)
+        ts = []
+        for i in range(reps):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            ctx.gather(d, n, r, g.camera, prm, o0, None, None, noise=noise)
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts[3:])
+
+    rows = []
+    for radius, ns, paper_gtao, paper_bm in [(0.8, 8, 0.49, 0.51), (1.0, 12, 0.75, 0.77), (1.0, 16, 0.95, 0.97),
+                                            (2.0, 16, 1.12, 1.13), (3.0, 16, 1.12, 1.13)]:
+        row = {"table": 1, "radius": radius, "steps_per_side": ns}
+        for name, t, nb in [("horizon_t_inf", math.inf, 32), ("bitmask_nb32", 0.5, 32), ("bitmask_nb128", 0.5, 128)]:
+            prm = scenegen.Params(1, ns, radius, t, sector_count=nb, gi=False)
+            row[name + "_ms"] = time_one("full", prm)
+        row["paper_rtx2080_ms"] = {"gtao": paper_gtao, "bitmask": paper_bm}
+        rows.append(row)
+    for label, ns, radius, mode, res, paper in [("a", 8, 1.0, 0, "full", 0.9), ("b", 8, 4.0, 0, "full", 1.7),
+                                                ("c", 16, 4.0, 0, "full", 2.3), ("d", 16, 4.0, 1, "full", 2.6),
+                                                ("e", 32, 4.0, 1, "full", 4.0), ("f", 16, 4.0, 1, "half", 0.97)]:
+        prm = scenegen.Params(1, ns, radius, 0.2, step_mode=mode)
+        rows.append({"table": 2, "config": label, "steps_per_side": ns, "radius": radius,
+                     "steps": "quadratic" if mode else "constant", "resolution": res,
+                     "ms": time_one(res, prm), "paper_rtx2080_sampling_ms": paper})
+    out = {"metric": "trend sweep (ms per 1080p frame)", "value": rows[2]["bitmask_nb32_ms"], "unit": "ms",
+           "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+           "config": {"workload": "1920x1080 seed 2, 64 spheres + 16 panels, fp32, N_d 1 with 4x4 IGN rotation",
+                      "l2": "flushed between timed runs"}, "rows": rows}
+    print(json.dumps(out))
+
+
 def run_serve_bench(args, world, rank, local):
     """Poisson stream (mean 2000 req/s) of frames 720p..4K, N_d 1-8, N_b 32/64, N_s 8/16/32, on
     resident G-buffers (2 seeds per size): continuous-batching server vs one launch + host sync
@@ -362,6 +423,9 @@ def main():
         return
     if args.workload == "serve":
         run_serve_bench(args, world, rank, local)
+        return
+    if args.workload == "trends":
+        run_trend_sweep(args, world, rank, local)
         return
     import torch
 

@@ -49,7 +49,7 @@ typedef struct ssilvb_ctx ssilvb_ctx; /* opaque, owned by the library */
 typedef enum {
     SSILVB_OK = 0,
     SSILVB_ERR_INVALID_ARG = 1,   /* null pointer, bad size, alignment or pitch, parameter out of range */
-    SSILVB_ERR_UNSUPPORTED = 2,   /* valid request this build does not implement (e.g. N_b = 128) */
+    SSILVB_ERR_UNSUPPORTED = 2,   /* valid request this build does not implement (e.g. mixed formats) */
     SSILVB_ERR_OUT_OF_MEMORY = 3, /* a context allocation failed */
     SSILVB_ERR_CUDA = 4,          /* a CUDA runtime or driver call failed; see ssilvb_last_error */
     SSILVB_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up */
@@ -95,7 +95,7 @@ typedef struct {
     float radius;          /* R > 0 (view-space units): projected radius r = R fx / z pixels */
     float thickness;       /* t > 0; +INF = infinite thickness (horizon-based occlusion) */
     float thickness_slope; /* k_t >= 0: thickness grows linearly with depth, t(z) = t + k_t z */
-    int sector_count;      /* N_b: 32 or 64 */
+    int sector_count;      /* N_b: 32, 64 or 128 (Section 4.1 compares 32 and 128) */
     int hit_rule;          /* 0: a sector is occluded when at least half covered (Section 3.1);
                               1: floor/ceil run of Algorithm 1 */
     int step_mode;         /* 0: constant steps r (j+1+xi_s)/(N_s+1);
@@ -114,7 +114,8 @@ typedef struct {
  * out1 (required iff ambient_cones > 0): float4 = (ambient.r, .g, .b, 0).
  * Pitches in bytes, multiples of 16; bases 16-byte aligned.
  * masks (optional, NULL = not written): the final slice bitmasks, dense
- * [num_slices][height][width] of uint32 (N_b = 32) or uint64 (N_b = 64), 8-byte aligned.
+ * [num_slices][height][width] of uint32 (N_b = 32), uint64 (N_b = 64) or 4 x uint32 (N_b = 128,
+ * sector k in bit k % 32 of word k / 32), aligned to that element size.
  * light_out (optional, NULL = not written): the light buffer for the next frame of the
  * multi-bounce scheme of Section 4.3, direct + bounce_gain * GI per channel (4th = 0), where
  * direct is gbuffer->direct (or the radiance plane when that is NULL), in the radiance plane's

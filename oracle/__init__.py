@@ -67,6 +67,10 @@ def _load():
         lib.orc32_sector_mask.restype = ctypes.c_uint64
         lib.orc64_sector_mask.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int]
         lib.orc64_sector_mask.restype = ctypes.c_uint64
+        lib.orc32_sector_mask_words.argtypes = [ctypes.c_float, ctypes.c_float, ctypes.c_int, ctypes.c_int,
+                                                ctypes.c_void_p]
+        lib.orc64_sector_mask_words.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                                ctypes.c_void_p]
         lib.orc32_acos_sweep.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
         lib.orc32_rsqrt_sweep.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int]
         lib.orc32_rsqrt_sweep.restype = ctypes.c_double
@@ -107,6 +111,7 @@ class Problem:
         self.c = p
         self.shape = (H, W)
         self.nd = params.num_slices
+        self.words = 2 if params.sector_count == 128 else 1
 
 
 def all_pixels(H: int, W: int) -> np.ndarray:
@@ -122,16 +127,16 @@ def _pixels(prob: Problem, pixels):
 
 def fp64(prob: Problem, pixels=None):
     """FP64 oracle on the listed (x, y) pixels (all when None).
-    Returns out0 [n,4], out1 [n,4], masks [n,N_d] uint64, margin [n,N_d]."""
+    Returns out0 [n,4], out1 [n,4], masks [n,N_d] uint64 ([n,N_d,2] for N_b = 128), margin [n,N_d]."""
     xy = _pixels(prob, pixels)
     n = xy.shape[0]
     o0 = np.zeros((n, 4)); o1 = np.zeros((n, 4))
-    m = np.zeros((n, prob.nd), dtype=np.uint64); g = np.zeros((n, prob.nd))
+    m = np.zeros((n, prob.nd, prob.words), dtype=np.uint64); g = np.zeros((n, prob.nd))
     rc = _load().orc64_pixels(ctypes.byref(prob.c), n, xy.ctypes.data, o0.ctypes.data, o1.ctypes.data,
                               m.ctypes.data, g.ctypes.data)
     if rc != 0:
         raise ValueError(f"orc64_pixels rejected the problem (code {rc})")
-    return o0, o1, m, g
+    return o0, o1, (m[..., 0] if prob.words == 1 else m), g
 
 
 def fp32(prob: Problem, pixels=None, counts: bool = False):
@@ -139,12 +144,13 @@ def fp32(prob: Problem, pixels=None, counts: bool = False):
     xy = _pixels(prob, pixels)
     n = xy.shape[0]
     o0 = np.zeros((n, 4), dtype=np.float32); o1 = np.zeros((n, 4), dtype=np.float32)
-    m = np.zeros((n, prob.nd), dtype=np.uint64)
+    m = np.zeros((n, prob.nd, prob.words), dtype=np.uint64)
     c = np.zeros(7, dtype=np.int64)
     rc = _load().orc32_pixels(ctypes.byref(prob.c), n, xy.ctypes.data, o0.ctypes.data, o1.ctypes.data,
                               m.ctypes.data, c.ctypes.data)
     if rc != 0:
         raise ValueError(f"orc32_pixels rejected the problem (code {rc})")
+    m = m[..., 0] if prob.words == 1 else m
     if counts:
         return o0, o1, m, dict(zip(["pixels", "sky", "slices", "samples", "skipped", "gi_fetches", "ops"], c.tolist()))
     return o0, o1, m
@@ -164,6 +170,16 @@ def sector_mask32(A: float, B: float, nb: int, rule: int = 0) -> int:
 
 def sector_mask64(A: float, B: float, nb: int, rule: int = 0) -> int:
     return int(_load().orc64_sector_mask(A, B, nb, rule))
+
+
+def sector_mask_words(A: float, B: float, nb: int, rule: int = 0, fp64: bool = False) -> int:
+    """The whole mask (up to 128 bits) as a Python int, from the replica or the FP64 oracle."""
+    out = np.zeros(2, dtype=np.uint64)
+    if fp64:
+        _load().orc64_sector_mask_words(A, B, nb, rule, out.ctypes.data)
+    else:
+        _load().orc32_sector_mask_words(A, B, nb, rule, out.ctypes.data)
+    return int(out[0]) | (int(out[1]) << 64)
 
 
 def acos32_sweep(stride: int = 16):

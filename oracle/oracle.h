@@ -29,7 +29,7 @@ typedef struct {
     float view_to_world[9]; /* row-major rotation, used only for the ambient SH lookup */
     int num_slices;         /* N_d */
     int steps_per_side;     /* N_s */
-    int sector_count;       /* N_b in {32, 64} */
+    int sector_count;       /* N_b in {32, 64, 128} */
     int hit_rule;           /* 0 = at least half covered, 1 = floor/ceil of Algorithm 1 */
     int step_mode;          /* 0 = constant steps, 1 = quadratic ("exponential") steps */
     float radius;           /* R, metres */
@@ -42,7 +42,8 @@ typedef struct {
 } orc_problem;
 
 /* Per pixel listed in xy ([n*2] = x, y): out0[4] = (GI.rgb, AO), out1[4] = (ambient.rgb, 0),
- * masks[N_d] (low N_b bits used), margin[N_d] = smallest distance, in sector units, of any
+ * masks[N_d][words] (words = 2 for N_b = 128, else 1; sector k is bit k % 64 of word k / 64),
+ * margin[N_d] = smallest distance, in sector units, of any
  * hit-rule decision of that slice from its rounding boundary.  Any output pointer may be NULL.
  * Returns 0, or a nonzero code for an invalid problem. */
 int orc64_pixels(const orc_problem *pb, int n, const int32_t *xy, double *out0, double *out1,
@@ -63,7 +64,10 @@ uint64_t orc32_sector_mask(float A, float B, int nb, int hit_rule);
 /* Test helpers (replica_fp32.c): exhaustive arccosine sweep over [0, 1] and rsqrt error sweep. */
 void orc32_acos_sweep(int stride, double *max_err, int64_t *increases);
 double orc32_rsqrt_sweep(double lo, double hi, int n);
-/* The FP64 oracle's per-sector brute-force mask, for tests. */
+/* The FP64 oracle's per-sector brute-force mask, for tests (first word; all words). */
 uint64_t orc64_sector_mask(double A, double B, int nb, int hit_rule);
+void orc64_sector_mask_words(double A, double B, int nb, int hit_rule, uint64_t *out2);
+/* The replica's O(1) mask as two 64-bit words, for tests. */
+void orc32_sector_mask_words(float A, float B, int nb, int hit_rule, uint64_t *out2);
 
 #endif

@@ -67,29 +67,49 @@ static d3 unproject(const orc_problem *pb, double u, double v, double z) {
     return mk((u - pb->cx) / pb->fx * z, -(v - pb->cy) / pb->fy * z, -z);
 }
 
-/* Per-sector hit rule, brute force over the N_b sectors [k, k+1). */
-uint64_t orc64_sector_mask(double A, double B, int nb, int hit_rule) {
-    uint64_t m = 0;
+/* Per-sector hit rule, brute force over the N_b sectors [k, k+1): set[k] = 1 when covered. */
+static void sector_set(double A, double B, int nb, int hit_rule, unsigned char *set) {
     if (hit_rule == 0) {
         for (int k = 0; k < nb; ++k) {
             double lo = A > k ? A : (double)k;
             double hi = B < k + 1 ? B : (double)(k + 1);
-            if (hi - lo >= 0.5) m |= (uint64_t)1 << k;
+            set[k] = hi - lo >= 0.5;
         }
     } else {
         /* Algorithm 1: a = floor(A), width = ceil(B - A), kept inside the N_b sectors */
         double a = floor(A);
         double w = ceil(B - A);
-        for (int k = 0; k < nb; ++k)
-            if (k >= a && k < a + w) m |= (uint64_t)1 << k;
+        for (int k = 0; k < nb; ++k) set[k] = k >= a && k < a + w;
     }
-    return m;
+}
+
+void orc64_sector_mask_words(double A, double B, int nb, int hit_rule, uint64_t *out2) {
+    unsigned char set[128];
+    sector_set(A, B, nb, hit_rule, set);
+    out2[0] = out2[1] = 0;
+    for (int k = 0; k < nb; ++k)
+        if (set[k]) out2[k / 64] |= (uint64_t)1 << (k % 64);
+}
+
+uint64_t orc64_sector_mask(double A, double B, int nb, int hit_rule) {
+    uint64_t w[2];
+    orc64_sector_mask_words(A, B, nb, hit_rule, w);
+    return w[0];
 }
 
 static double frac_dist(double v) { return fabs(v - nearbyint(v)); }
 
-/* Distance of this sample's hit-rule decisions from their rounding boundaries. */
-static double decision_margin(double A, double B, int hit_rule) {
+/* Distance of this sample's hit-rule decisions from their rounding boundaries, in sector
+ * units.  rawA, rawB: the endpoints before clamping to [0, N_b].  An endpoint pinned by the
+ * clamp cannot move until its unclamped value comes back inside, so for it the distance is
+ * how far the unclamped value lies beyond the edge, not its distance to an integer. */
+static double pinned(double raw, double nb) {
+    if (raw > nb) return raw - nb;
+    if (raw < 0.0) return -raw;
+    return -1.0; /* not pinned */
+}
+
+static double decision_margin(double A, double B, double rawA, double rawB, int nb, int hit_rule) {
     if (hit_rule == 0) {
         double m = fabs((B - A) - 0.5);
         double ma = frac_dist(A - 0.5), mb = frac_dist(B + 0.5);
@@ -97,8 +117,9 @@ static double decision_margin(double A, double B, int hit_rule) {
         if (mb < m) m = mb;
         return m;
     }
-    double m = frac_dist(A);
-    double mw = frac_dist(B - A);
+    const double pa = pinned(rawA, nb), pb = pinned(rawB, nb);
+    double m = pa >= 0.0 ? pa : frac_dist(A);
+    double mw = (pa >= 0.0 && pb >= 0.0 && A == B) ? (pa < pb ? pa : pb) : frac_dist(B - A);
     return mw < m ? mw : m;
 }
 
@@ -125,7 +146,7 @@ static int validate(const orc_problem *pb) {
     if (!pb || pb->width <= 0 || pb->height <= 0 || !pb->depth || !pb->normal || !pb->radiance) return 1;
     if (pb->num_slices < 1 || pb->num_slices > 16) return 2;
     if (pb->steps_per_side < 1 || pb->steps_per_side > 64) return 3;
-    if (pb->sector_count != 32 && pb->sector_count != 64) return 4;
+    if (pb->sector_count != 32 && pb->sector_count != 64 && pb->sector_count != 128) return 4;
     if (pb->hit_rule != 0 && pb->hit_rule != 1) return 5;
     if (!(pb->radius > 0.0f) || !(pb->radius < INFINITY)) return 6;
     if (!(pb->thickness > 0.0f) || !(pb->thickness_slope >= 0.0f) || !(pb->thickness_slope < INFINITY)) return 7;
@@ -141,6 +162,7 @@ int orc64_pixels(const orc_problem *pb, int n, const int32_t *xy, double *out0, 
     if (bad) return bad;
     const int W = pb->width, H = pb->height, nd = pb->num_slices, ns = pb->steps_per_side;
     const int nb = pb->sector_count, na = pb->ambient_cones;
+    const int words = nb == 128 ? 2 : 1;
     const int inf_t = isinf(pb->thickness);
 
     for (int pi = 0; pi < n; ++pi) {
@@ -155,7 +177,8 @@ int orc64_pixels(const orc_problem *pb, int n, const int32_t *xy, double *out0, 
             if (o0) { o0[0] = o0[1] = o0[2] = 0.0; o0[3] = 1.0; }
             if (o1) { o1[0] = o1[1] = o1[2] = o1[3] = 0.0; }
             for (int i = 0; i < nd; ++i) {
-                if (masks) masks[(size_t)pi * nd + i] = 0;
+                if (masks)
+                    for (int w = 0; w < words; ++w) masks[((size_t)pi * nd + i) * words + w] = 0;
                 if (margin) margin[(size_t)pi * nd + i] = INFINITY;
             }
             continue;
@@ -199,7 +222,7 @@ int orc64_pixels(const orc_problem *pb, int n, const int32_t *xy, double *out0, 
                 if (nsd < 0.0) gamma = -gamma;
             }
 
-            unsigned char occ[64];
+            unsigned char occ[128];
             memset(occ, 0, sizeof(occ));
             double mrg = INFINITY;
 
@@ -232,26 +255,29 @@ int orc64_pixels(const orc_problem *pb, int n, const int32_t *xy, double *out0, 
                     const double llen = len3(l);
                     const double hf = sigma * acos(clampd(dot3(l, vhat) / llen, -1.0, 1.0));
                     const double K = nb / M_PI;
-                    double Xf = clampd((hf - gamma) * K + 0.5 * nb, 0.0, (double)nb);
-                    double Xb;
+                    const double Xf_raw = (hf - gamma) * K + 0.5 * nb;
+                    double Xb_raw;
                     if (inf_t) {
-                        Xb = sigma > 0 ? (double)nb : 0.0;
+                        Xb_raw = sigma > 0 ? INFINITY : -INFINITY;
                     } else {
                         /* Back sample s_b = s_f + t p/|p| (behind the front one). */
                         const d3 sb = add3(sf, mul3(p, tp / plen));
                         const d3 lb = sub3(sb, p);
                         const double hb = sigma * acos(clampd(dot3(lb, vhat) / len3(lb), -1.0, 1.0));
-                        Xb = clampd((hb - gamma) * K + 0.5 * nb, 0.0, (double)nb);
+                        Xb_raw = (hb - gamma) * K + 0.5 * nb;
                     }
+                    const double Xf = clampd(Xf_raw, 0.0, (double)nb), Xb = clampd(Xb_raw, 0.0, (double)nb);
                     const double A = Xf < Xb ? Xf : Xb, B = Xf < Xb ? Xb : Xf;
-                    const uint64_t bj = orc64_sector_mask(A, B, nb, pb->hit_rule);
-                    const double m = decision_margin(A, B, pb->hit_rule);
+                    const double rawA = Xf < Xb ? Xf_raw : Xb_raw, rawB = Xf < Xb ? Xb_raw : Xf_raw;
+                    unsigned char bj[128];
+                    sector_set(A, B, nb, pb->hit_rule, bj);
+                    const double m = decision_margin(A, B, rawA, rawB, nb, pb->hit_rule);
                     if (m < mrg) mrg = m;
 
                     /* Indirect light: each newly occluded sector carries c_j cos cos / N_b. */
                     int newly = 0;
                     for (int k = 0; k < nb; ++k)
-                        if (((bj >> k) & 1u) && !occ[k]) { occ[k] = 1; ++newly; }
+                        if (bj[k] && !occ[k]) { occ[k] = 1; ++newly; }
                     if (newly > 0 && pb->gi) {
                         const float *cj = pb->radiance + 4 * q;
                         const float *nj = pb->normal + 4 * q;
@@ -290,10 +316,10 @@ int orc64_pixels(const orc_problem *pb, int n, const int32_t *xy, double *out0, 
             }
 
             if (masks) {
-                uint64_t bm = 0;
+                uint64_t bm[2] = {0, 0};
                 for (int k = 0; k < nb; ++k)
-                    if (occ[k]) bm |= (uint64_t)1 << k;
-                masks[(size_t)pi * nd + i] = bm;
+                    if (occ[k]) bm[k / 64] |= (uint64_t)1 << (k % 64);
+                for (int w = 0; w < words; ++w) masks[((size_t)pi * nd + i) * words + w] = bm[w];
             }
             if (margin) margin[(size_t)pi * nd + i] = mrg;
         }

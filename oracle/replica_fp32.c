@@ -68,9 +68,16 @@ float orc32_acos(float c) {
     return c < 0.0f ? 3.14159265358979323846f - r : r;
 }
 
-static uint64_t low_bits(int k) { return k >= 64 ? ~(uint64_t)0 : (((uint64_t)1 << k) - 1); }
+/* Sector masks of up to 128 bits. */
+typedef unsigned __int128 mask_t;
 
-uint64_t orc32_sector_mask(float A, float B, int nb, int hit_rule) {
+static mask_t low_bits(int k) { return k >= 128 ? ~(mask_t)0 : (((mask_t)1 << k) - 1); }
+
+static int popc128(mask_t v) {
+    return __builtin_popcountll((uint64_t)v) + __builtin_popcountll((uint64_t)(v >> 64));
+}
+
+static mask_t sector_run(float A, float B, int nb, int hit_rule) {
     int lo, hi;
     if (hit_rule == 0) {
         /* sectors whose centre k + 1/2 lies in [A, B], provided B - A >= 1/2:
@@ -87,13 +94,23 @@ uint64_t orc32_sector_mask(float A, float B, int nb, int hit_rule) {
     return low_bits(hi) & ~low_bits(lo);
 }
 
+uint64_t orc32_sector_mask(float A, float B, int nb, int hit_rule) {
+    return (uint64_t)sector_run(A, B, nb, hit_rule);
+}
+
+void orc32_sector_mask_words(float A, float B, int nb, int hit_rule, uint64_t *out2) {
+    const mask_t m = sector_run(A, B, nb, hit_rule);
+    out2[0] = (uint64_t)m;
+    out2[1] = (uint64_t)(m >> 64);
+}
+
 static int is_geometry(float z) { return z > 0.0f && z < INFINITY; }
 
 static int validate(const orc_problem *pb) {
     if (!pb || pb->width <= 0 || pb->height <= 0 || !pb->depth || !pb->normal || !pb->radiance) return 1;
     if (pb->num_slices < 1 || pb->num_slices > 16) return 2;
     if (pb->steps_per_side < 1 || pb->steps_per_side > 64) return 3;
-    if (pb->sector_count != 32 && pb->sector_count != 64) return 4;
+    if (pb->sector_count != 32 && pb->sector_count != 64 && pb->sector_count != 128) return 4;
     if (pb->hit_rule != 0 && pb->hit_rule != 1) return 5;
     if (!(pb->radius > 0.0f) || !(pb->radius < INFINITY)) return 6;
     if (!(pb->thickness > 0.0f) || !(pb->thickness_slope >= 0.0f) || !(pb->thickness_slope < INFINITY)) return 7;
@@ -109,6 +126,7 @@ int orc32_pixels(const orc_problem *pb, int n, const int32_t *xy, float *out0, f
     if (bad) return bad;
     const int W = pb->width, H = pb->height, nd = pb->num_slices, ns = pb->steps_per_side;
     const int nb = pb->sector_count, na = pb->ambient_cones;
+    const int words = nb == 128 ? 2 : 1;
     const int inf_t = isinf(pb->thickness);
     int64_t c_pix = 0, c_sky = 0, c_slice = 0, c_visit = 0, c_skip = 0, c_gi = 0, ops = 0;
 
@@ -161,7 +179,8 @@ int orc32_pixels(const orc_problem *pb, int n, const int32_t *xy, float *out0, f
             ops += 8;
             if (o0) { o0[0] = o0[1] = o0[2] = 0.0f; o0[3] = 1.0f; }
             if (o1) { o1[0] = o1[1] = o1[2] = o1[3] = 0.0f; }
-            if (masks) for (int i = 0; i < nd; ++i) masks[(size_t)pi * nd + i] = 0;
+            if (masks)
+                for (int i = 0; i < nd * words; ++i) masks[(size_t)pi * nd * words + i] = 0;
             continue;
         }
 
@@ -223,7 +242,7 @@ int orc32_pixels(const orc_problem *pb, int n, const int32_t *xy, float *out0, f
             const float thr2_p = thr_p * thr_p, thr2_m = thr_m * thr_m;
             ops += 2 + 2 + 3 + 3 + RSQRT_OPS + 3 + 6 + 2 + 1 + 1 + 2 + 8 + 8 + 2;
 
-            uint64_t b = 0;
+            mask_t b = 0;
             for (int side = 0; side < 2; ++side) {
                 const int pos = side == 1; /* side -omega first, then +omega */
                 const float wsx = pos ? cphi : -cphi, wsy = pos ? sphi : -sphi;
@@ -289,8 +308,8 @@ int orc32_pixels(const orc_problem *pb, int n, const int32_t *xy, float *out0, f
                     /* The back endpoint lies toward this side's edge: [A, B] = [X_f, X_b] on side +,
                      * [X_b, X_f] on side - (a rounding-level reversal leaves B < A: no sector). */
                     const float A = pos ? Xf : Xb, B = pos ? Xb : Xf;
-                    const uint64_t bj = orc32_sector_mask(A, B, nb, pb->hit_rule);
-                    const int newly = __builtin_popcountll(bj & ~b);
+                    const mask_t bj = sector_run(A, B, nb, pb->hit_rule);
+                    const int newly = popc128(bj & ~b);
                     b |= bj;
                     ops += 12 + 3 + 1;
 
@@ -310,13 +329,13 @@ int orc32_pixels(const orc_problem *pb, int n, const int32_t *xy, float *out0, f
             }
 
             /* Slice end: unoccluded fraction, then the ambient cones (Section 3.2). */
-            const int occ = __builtin_popcountll(b);
+            const int occ = popc128(b);
             AO += (float)(nb - occ) * inv_nb;
             ops += 5;
             for (int k = 0; k < na; ++k) {
                 const int g = nb / na;
-                const uint64_t Mk = low_bits((k + 1) * g) & ~low_bits(k * g);
-                const int freek = __builtin_popcountll(~b & Mk);
+                const mask_t Mk = low_bits((k + 1) * g) & ~low_bits(k * g);
+                const int freek = popc128(~b & Mk);
                 const float ck = fmaf(cg, ccos[k], -(sg * csin[k]));
                 const float sk = fmaf(sg, ccos[k], cg * csin[k]);
                 const float ax3 = fmaf(ck, vx, sk * sx), ay3 = fmaf(ck, vy, sk * sy), az3 = fmaf(ck, vz, sk * sz);
@@ -346,7 +365,10 @@ int orc32_pixels(const orc_problem *pb, int n, const int32_t *xy, float *out0, f
                 AMb = fmaf(wt, L[2], AMb);
                 ops += 3 + 4 + 6 + 9 + 17 + 2 + 27 + 3;
             }
-            if (masks) masks[(size_t)pi * nd + i] = b;
+            if (masks) {
+                masks[((size_t)pi * nd + i) * words] = (uint64_t)b;
+                if (words == 2) masks[((size_t)pi * nd + i) * words + 1] = (uint64_t)(b >> 64);
+            }
         }
         if (o0) { o0[0] = GIr * inv_nd; o0[1] = GIg * inv_nd; o0[2] = GIb * inv_nd; o0[3] = AO * inv_nd; }
         if (o1) { o1[0] = AMr * inv_nd; o1[1] = AMg * inv_nd; o1[2] = AMb * inv_nd; o1[3] = 0.0f; }

@@ -37,7 +37,7 @@ def _sources():
     return [os.path.join(_CSRC, f) for f in sorted(os.listdir(_CSRC))] + [os.path.join(INCLUDE, "ssilvb.h")]
 
 
-UNITS = ["ssilvb.cu", "batch.cu", "launch_nb32.cu", "launch_nb64.cu", "noalloc.cu"]
+UNITS = ["ssilvb.cu", "batch.cu", "launch_nb32.cu", "launch_nb64.cu", "launch_nb128.cu", "noalloc.cu"]
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
@@ -357,6 +357,6 @@ def alloc_outputs(H: int, W: int, params, device="cuda", masks: bool = False):
     out1 = torch.empty((H, W, 4), dtype=torch.float32, device=device) if params.ambient_cones > 0 else None
     m = None
     if masks:
-        m = torch.empty((params.num_slices, H, W), dtype=torch.int32 if params.sector_count == 32 else torch.int64,
-                        device=device)
+        words = {32: 1, 64: 2, 128: 4}[params.sector_count]
+        m = torch.empty((params.num_slices, H, W, words), dtype=torch.int32, device=device)
     return out0, out1, m

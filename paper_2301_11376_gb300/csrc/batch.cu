@@ -77,16 +77,12 @@ cudaError_t enqueue_batch(ssilvb_ctx *ctx, BatchSlot &s, size_t bytes, int nb, b
     const FrameDesc *frames = reinterpret_cast<const FrameDesc *>(s.d_table + sizeof(BatchHeader));
     cudaError_t e = cudaMemcpyAsync(s.d_table, s.h_table, bytes, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(s.d_queue, 0, sizeof(unsigned), st);
-    if (e == cudaSuccess)
-        e = nb == 32 ? launch_batch_nb32(hdr, frames, s.d_queue, f16, inf_t, sm, k, grid, st)
-                     : launch_batch_nb64(hdr, frames, s.d_queue, f16, inf_t, sm, k, grid, st);
+    if (e == cudaSuccess) e = launch_batch_nb(nb, hdr, frames, s.d_queue, f16, inf_t, sm, k, grid, st);
     (void)ctx;
     return e;
 }
 
-int occupancy(int nb, bool f16, bool inf_t, int minb) {
-    return nb == 32 ? batch_occ_nb32(f16, inf_t, minb) : batch_occ_nb64(f16, inf_t, minb);
-}
+int occupancy(int nb, bool f16, bool inf_t, int minb) { return batch_occ(nb, f16, inf_t, minb); }
 
 ssilvb_status run_batch(ssilvb_ctx *ctx, const ssilvb_frame *frames, int n, cudaStream_t st, const KernelChoice *force) {
     if (!frames || n < 1 || n > kMaxFrames)

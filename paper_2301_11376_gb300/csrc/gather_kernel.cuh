@@ -109,9 +109,31 @@ __device__ __forceinline__ uint32_t run32(int lo, int cnt) {
     return r;
 }
 
+// 128 sectors: four 32-bit words, sector k in bit k % 32 of word k / 32.
+struct Mask128 {
+    uint32_t w[4];
+    __device__ __forceinline__ Mask128() {}
+    __device__ __forceinline__ Mask128(int zero) { w[0] = w[1] = w[2] = w[3] = (uint32_t)zero; }
+    __device__ __forceinline__ Mask128 operator&(const Mask128 &o) const {
+        Mask128 r;
+        for (int i = 0; i < 4; ++i) r.w[i] = w[i] & o.w[i];
+        return r;
+    }
+    __device__ __forceinline__ Mask128 operator~() const {
+        Mask128 r;
+        for (int i = 0; i < 4; ++i) r.w[i] = ~w[i];
+        return r;
+    }
+    __device__ __forceinline__ Mask128 &operator|=(const Mask128 &o) {
+        for (int i = 0; i < 4; ++i) w[i] |= o.w[i];
+        return *this;
+    }
+};
+
 template <int NB> struct MaskT;
 template <> struct MaskT<32> { using T = uint32_t; };
 template <> struct MaskT<64> { using T = unsigned long long; };
+template <> struct MaskT<128> { using T = Mask128; };
 
 template <int NB> __device__ __forceinline__ typename MaskT<NB>::T run_mask(int lo, int hi);
 template <> __device__ __forceinline__ uint32_t run_mask<32>(int lo, int hi) { return run32(lo, hi - lo); }
@@ -123,8 +145,21 @@ template <> __device__ __forceinline__ unsigned long long run_mask<64>(int lo, i
     return ((unsigned long long)w1 << 32) | w0;
 }
 
+template <> __device__ __forceinline__ Mask128 run_mask<128>(int lo, int hi) {
+    Mask128 r;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int a = min(max(lo - 32 * i, 0), 32), e = min(max(hi - 32 * i, 0), 32);
+        r.w[i] = run32(a, max(e - a, 0));
+    }
+    return r;
+}
+
 __device__ __forceinline__ int popc_(uint32_t v) { return __popc(v); }
 __device__ __forceinline__ int popc_(unsigned long long v) { return __popcll(v); }
+__device__ __forceinline__ int popc_(const Mask128 &v) {
+    return __popc(v.w[0]) + __popc(v.w[1]) + __popc(v.w[2]) + __popc(v.w[3]);
+}
 
 // Sector run of a sample with endpoints A <= B (sector units, already in [0, N_b]).
 template <int NB>

@@ -31,6 +31,16 @@ cudaError_t launch_batch_nb32(const BatchHeader *hdr, const FrameDesc *frames, u
                               int step_mode, const KernelChoice &k, int grid, cudaStream_t s);
 cudaError_t launch_batch_nb64(const BatchHeader *hdr, const FrameDesc *frames, unsigned *queue, bool f16, bool inf_t,
                               int step_mode, const KernelChoice &k, int grid, cudaStream_t s);
+cudaError_t launch_single_nb128(const GatherParams &P, bool f16, bool inf_t, const KernelChoice &k, cudaStream_t s);
+cudaError_t launch_batch_nb128(const BatchHeader *hdr, const FrameDesc *frames, unsigned *queue, bool f16, bool inf_t,
+                               int step_mode, const KernelChoice &k, int grid, cudaStream_t s);
+int batch_occ_nb128(bool f16, bool inf_t, int minb);
+void single_node_nb128(const GatherParams &P, bool f16, bool inf_t, const KernelChoice &k, const void **fn, dim3 *grid,
+                       dim3 *block);
+// Dispatch on the sector count (32, 64 or 128).
+cudaError_t launch_batch_nb(int nb, const BatchHeader *hdr, const FrameDesc *frames, unsigned *queue, bool f16,
+                            bool inf_t, int step_mode, const KernelChoice &k, int grid, cudaStream_t s);
+int batch_occ(int nb, bool f16, bool inf_t, int minb);
 // The single-frame kernel of a variant and its launch shape (for graph kernel nodes).
 void single_kernel_node(const GatherParams &P, int nb, bool f16, bool inf_t, const KernelChoice &k, const void **fn,
                         dim3 *grid, dim3 *block);

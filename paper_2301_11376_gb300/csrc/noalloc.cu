@@ -107,7 +107,7 @@ extern "C" ssilvb_status ssilvb_gather_batch_noalloc(const ssilvb_frame *frames,
     int sms = 0, per_sm = 0;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaDeviceGetAttribute");
-    per_sm = nb == 32 ? batch_occ_nb32(f16, inf_t, k.minb) : batch_occ_nb64(f16, inf_t, k.minb);
+    per_sm = batch_occ(nb, f16, inf_t, k.minb);
     const int grid = std::max(1, std::max(1, per_sm) * sms);
 
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -121,8 +121,7 @@ extern "C" ssilvb_status ssilvb_gather_batch_noalloc(const ssilvb_frame *frames,
     const BatchHeader *d_hdr = reinterpret_cast<const BatchHeader *>(base);
     const FrameDesc *d_frames = reinterpret_cast<const FrameDesc *>(base + sizeof(BatchHeader));
     unsigned *d_queue = reinterpret_cast<unsigned *>(base + kQueueOffset);
-    e = nb == 32 ? launch_batch_nb32(d_hdr, d_frames, d_queue, f16, inf_t, sm, k, grid, s)
-                 : launch_batch_nb64(d_hdr, d_frames, d_queue, f16, inf_t, sm, k, grid, s);
+    e = launch_batch_nb(nb, d_hdr, d_frames, d_queue, f16, inf_t, sm, k, grid, s);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch launch");
     return SSILVB_OK;
 }

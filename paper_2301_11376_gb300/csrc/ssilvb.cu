@@ -75,9 +75,8 @@ ssilvb_status validate(ssilvb_ctx *ctx, const ssilvb_gbuffer *g, const ssilvb_ca
         return fail(ctx, SSILVB_ERR_INVALID_ARG, "thickness must be in (0, 1e6] or +INF");
     if (!(p->thickness_slope >= 0.0f) || !std::isfinite(p->thickness_slope))
         return fail(ctx, SSILVB_ERR_INVALID_ARG, "thickness_slope must be finite and >= 0");
-    if (p->sector_count == 128) return fail(ctx, SSILVB_ERR_UNSUPPORTED, "sector_count 128 is not built");
-    if (p->sector_count != 32 && p->sector_count != 64)
-        return fail(ctx, SSILVB_ERR_INVALID_ARG, "sector_count %d not in {32, 64}", p->sector_count);
+    if (p->sector_count != 32 && p->sector_count != 64 && p->sector_count != 128)
+        return fail(ctx, SSILVB_ERR_INVALID_ARG, "sector_count %d not in {32, 64, 128}", p->sector_count);
     if (p->hit_rule != 0 && p->hit_rule != 1) return fail(ctx, SSILVB_ERR_INVALID_ARG, "hit_rule must be 0 or 1");
     if (p->step_mode != 0 && p->step_mode != 1) return fail(ctx, SSILVB_ERR_INVALID_ARG, "step_mode must be 0 or 1");
     if (p->compute_gi != 0 && p->compute_gi != 1) return fail(ctx, SSILVB_ERR_INVALID_ARG, "compute_gi must be 0 or 1");
@@ -97,7 +96,8 @@ ssilvb_status validate(ssilvb_ctx *ctx, const ssilvb_gbuffer *g, const ssilvb_ca
         return fail(ctx, SSILVB_ERR_INVALID_ARG, "out0 must be 16-byte aligned with pitch >= 16*width, multiple of 16");
     if (na > 0 && (!o->out1 || o->out1_pitch < W * 16 || o->out1_pitch % 16 || !aligned(o->out1, 16)))
         return fail(ctx, SSILVB_ERR_INVALID_ARG, "out1 (16-byte aligned, pitch >= 16*width) required with ambient cones");
-    if (o->masks && !aligned(o->masks, 8)) return fail(ctx, SSILVB_ERR_INVALID_ARG, "masks must be 8-byte aligned");
+    if (o->masks && !aligned(o->masks, p->sector_count == 128 ? 16 : 8))
+        return fail(ctx, SSILVB_ERR_INVALID_ARG, "masks must be aligned to their element size");
     if (o->light_out) {
         if (!aligned(o->light_out, 16) || o->light_out_pitch < W * px || o->light_out_pitch % px)
             return fail(ctx, SSILVB_ERR_INVALID_ARG, "light_out: 16-byte aligned, pitch a multiple of %zu >= width", px);
@@ -204,13 +204,29 @@ void fill_params(ssilvb::GatherParams &P, const ssilvb_gbuffer *g, const ssilvb_
 }
 
 cudaError_t launch_single(const GatherParams &P, int nb, bool f16, bool inf_t, const KernelChoice &k, cudaStream_t s) {
-    return nb == 32 ? launch_single_nb32(P, f16, inf_t, k, s) : launch_single_nb64(P, f16, inf_t, k, s);
+    if (nb == 32) return launch_single_nb32(P, f16, inf_t, k, s);
+    if (nb == 64) return launch_single_nb64(P, f16, inf_t, k, s);
+    return launch_single_nb128(P, f16, inf_t, k, s);
 }
 
 void single_kernel_node(const GatherParams &P, int nb, bool f16, bool inf_t, const KernelChoice &k, const void **fn,
                         dim3 *grid, dim3 *block) {
     if (nb == 32) single_node_nb32(P, f16, inf_t, k, fn, grid, block);
-    else single_node_nb64(P, f16, inf_t, k, fn, grid, block);
+    else if (nb == 64) single_node_nb64(P, f16, inf_t, k, fn, grid, block);
+    else single_node_nb128(P, f16, inf_t, k, fn, grid, block);
+}
+
+cudaError_t launch_batch_nb(int nb, const BatchHeader *hdr, const FrameDesc *frames, unsigned *queue, bool f16,
+                            bool inf_t, int step_mode, const KernelChoice &k, int grid, cudaStream_t s) {
+    if (nb == 32) return launch_batch_nb32(hdr, frames, queue, f16, inf_t, step_mode, k, grid, s);
+    if (nb == 64) return launch_batch_nb64(hdr, frames, queue, f16, inf_t, step_mode, k, grid, s);
+    return launch_batch_nb128(hdr, frames, queue, f16, inf_t, step_mode, k, grid, s);
+}
+
+int batch_occ(int nb, bool f16, bool inf_t, int minb) {
+    if (nb == 32) return batch_occ_nb32(f16, inf_t, minb);
+    if (nb == 64) return batch_occ_nb64(f16, inf_t, minb);
+    return batch_occ_nb128(f16, inf_t, minb);
 }
 
 TuneKey tune_key(const ssilvb_gbuffer *g, const ssilvb_params *p, int batch) {

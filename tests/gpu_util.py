@@ -1,14 +1,21 @@
 """Helpers shared by the GPU tests: run the CUDA gather through the C ABI and compare
-it with the CPU oracle (bitmasks bit-exact against the binary32 replica; AO, GI and
-ambient within 1e-4 of the FP64 oracle wherever the FP64 masks agree; every mask
-disagreement explained by an FP64 decision within 1e-3 sector units of its
-rounding boundary)."""
+it with the CPU oracle.
+
+Gates: (G1) bitmasks bit-exact against the binary32 replica; (G3) every FP64/binary32 mask
+disagreement explained by an FP64 decision within 1e-3 sector units of its rounding
+boundary; (G2) AO, GI and ambient within 1e-4 of the FP64 oracle on every pixel none of
+whose hit-rule decisions lies within 1e-4 sector units of a boundary.  On the remaining pixels the two
+precisions may credit a sector to different samples (GI credits each sector to the first
+sample that covers it) or flip it: there the difference is bounded by a few sectors' share,
+and such pixels must stay rare."""
 import numpy as np
 
 import oracle
 
 TOL = 1e-4          # absolute, AO / GI / ambient vs the FP64 oracle
-MARGIN_TOL = 1e-3   # sector units: binary32 endpoint error bound used to explain a mask flip
+MARGIN_TOL = 1e-3   # sector units: a mask flip must come from a decision this close to its boundary
+CLEAR_TOL = 1e-4    # sector units: decisions this far from every boundary agree in both precisions
+                    # (the largest binary32 endpoint error observed is ~3e-6 sector units)
 
 
 def to_device(g, pad: int = 0):
@@ -28,6 +35,17 @@ def to_device(g, pad: int = 0):
     return put(g.depth), put(g.normal), put(g.radiance)
 
 
+def masks_to_u64(m, nb):
+    """Device masks [N_d, H, W, words] (int32 words) -> [H*W, N_d] uint64, or [H*W, N_d, 2] for N_b = 128."""
+    a = np.ascontiguousarray(m.cpu().numpy()).view(np.uint32)
+    nd = a.shape[0]
+    if nb == 32:
+        return a.reshape(nd, -1).T.astype(np.uint64).copy()
+    if nb == 64:
+        return a.reshape(nd, -1, 2).copy().view(np.uint64).reshape(nd, -1).T.copy()
+    return a.reshape(nd, -1, 4).copy().view(np.uint64).reshape(nd, -1, 2).transpose(1, 0, 2).copy()
+
+
 def run_gpu(ctx, g, prm, noise=None, sh=None, pad: int = 0, stream=None):
     import torch
 
@@ -40,9 +58,7 @@ def run_gpu(ctx, g, prm, noise=None, sh=None, pad: int = 0, stream=None):
     torch.cuda.synchronize()
     o0 = out0.cpu().numpy().reshape(-1, 4).astype(np.float64)
     o1 = out1.cpu().numpy().reshape(-1, 4).astype(np.float64) if out1 is not None else None
-    mm = m.cpu().numpy().reshape(prm.num_slices, -1).T
-    mm = (mm.astype(np.uint32).astype(np.uint64) if prm.sector_count == 32 else mm.view(np.uint64)).copy()
-    return o0, o1, mm
+    return o0, o1, masks_to_u64(m, prm.sector_count)
 
 
 def pick(a, idx):
@@ -66,20 +82,32 @@ def check_parity(g, prm, noise, sh, gpu, pixels=None, min_agree=0.98):
     assert bad.size == 0, f"{len(bad)} bitmasks differ from the replica, first at pixel {xy[bad[0][0]]}"
     # G3: FP64 vs binary32 mask disagreements only at rounding boundaries
     diff = em != rm
+    if diff.ndim == 3:
+        diff = diff.any(axis=2)
     assert np.all(margin[diff] < MARGIN_TOL), f"unexplained mask flip, margin {margin[diff].max()}"
-    agree = np.all(em == rm, axis=1)
+    agree = ~diff.any(axis=1)
     assert agree.mean() >= min_agree, agree.mean()
-    # G2: continuous outputs within 1e-4 of FP64 where the masks agree
-    err0 = np.abs(g0[agree] - e0[agree]).max(initial=0.0)
+    # G2: continuous outputs within 1e-4 of FP64 where no decision is near a boundary
+    clear = agree & (margin.min(axis=1) >= CLEAR_TOL)
+    # the floor/ceil rule flips on samples lying in the tangent plane to rounding, so fewer of its
+    # pixels are far from every boundary; the fraction only guards against a vacuous comparison
+    assert clear.mean() >= (min_agree - 0.05 if prm.hit_rule == 0 else 0.7), clear.mean()
+    err0 = np.abs(g0[clear] - e0[clear]).max(initial=0.0)
     assert err0 <= TOL, err0
     if prm.ambient_cones > 0:
-        err1 = np.abs(g1[agree] - e1[agree]).max(initial=0.0)
+        err1 = np.abs(g1[clear] - e1[clear]).max(initial=0.0)
         assert err1 <= TOL, err1
+    # near-boundary pixels: at most a few sectors' share (radiance and cosines are <= 1)
+    near = ~clear
+    few = 4.0 / prm.sector_count + TOL
+    assert np.abs(g0[near] - e0[near]).max(initial=0.0) <= few
+    if prm.ambient_cones > 0:
+        assert np.abs(g1[near] - e1[near]).max(initial=0.0) <= 2.0 * few
     # GPU vs replica: the same binary32 sequence, so only accumulation-order effects remain
     assert np.abs(g0 - r0).max(initial=0.0) <= 1e-6
     if prm.ambient_cones > 0:
         assert np.abs(g1 - r1).max(initial=0.0) <= 1e-6
-    return {"agree": float(agree.mean()), "err_fp64": float(err0), "n": len(xy)}
+    return {"agree": float(agree.mean()), "clear": float(clear.mean()), "err_fp64": float(err0), "n": len(xy)}
 
 
 def sample_pixels(H, W, n, seed=0):

@@ -7,7 +7,7 @@ import pytest
 
 import scenegen
 from scenegen import Params
-from tests.gpu_util import run_gpu
+from tests.gpu_util import masks_to_u64, run_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -60,9 +60,7 @@ def _check_against_single(ctx, outs, gbs, prms):
         assert np.array_equal(got0, ref[0])
         if prm.ambient_cones:
             assert np.array_equal(o1.cpu().numpy().reshape(-1, 4).astype(np.float64), ref[1])
-        mm = m.cpu().numpy().reshape(prm.num_slices, -1).T
-        mm = mm.astype(np.uint32).astype(np.uint64) if prm.sector_count == 32 else mm.view(np.uint64)
-        assert np.array_equal(mm, ref[2])
+        assert np.array_equal(masks_to_u64(m, prm.sector_count), ref[2])
 
 
 UNEVEN = [
@@ -86,10 +84,11 @@ def test_batch_equals_single(ctx, mode, rows, graph):
     _check_against_single(ctx, outs, gbs, prms)
 
 
-def test_batch_fp16_nb64(ctx):
+@pytest.mark.parametrize("nb", [64, 128])
+def test_batch_fp16_wide_masks(ctx, nb):
     import torch
     specs = [(110 + i, 64 + 37 * i, 40 + 11 * i, dict(num_slices=1 + i % 4, steps_per_side=8 + 5 * i,
-                                                     sector_count=64, ambient_cones=8)) for i in range(5)]
+                                                     sector_count=nb, ambient_cones=8)) for i in range(5)]
     for mode in (1, 2):
         frames, keep, outs, gbs, prms = _frames(ctx, specs, f16=True)
         ctx.set_tuning(batch_mode=mode)

@@ -50,6 +50,9 @@ SMALL = [
     (64, 48, 12, dict(num_slices=2, steps_per_side=8, ambient_cones=1), False),
     (70, 33, 13, dict(num_slices=5, steps_per_side=7, sector_count=64, thickness=math.inf, hit_rule=1), True),
     (33, 70, 14, dict(num_slices=4, steps_per_side=10, sector_count=64, step_mode=1, ambient_cones=4), True),
+    (64, 48, 15, dict(num_slices=3, steps_per_side=12, sector_count=128, ambient_cones=8), True),
+    (45, 37, 16, dict(num_slices=2, steps_per_side=9, sector_count=128, thickness=math.inf, hit_rule=1), True),
+    (50, 41, 17, dict(num_slices=5, steps_per_side=7, sector_count=128, step_mode=1, thickness_slope=0.03), True),
 ]
 
 
@@ -122,7 +125,7 @@ def test_1080p_full_masks_and_sampled_fp64(ctx):
     check_parity(w.gbuf, w.params, w.noise, None, res, pixels=sample_pixels(H, W, 20000, 1))
 
 
-@pytest.mark.parametrize("nb", [32, 64])
+@pytest.mark.parametrize("nb", [32, 64, 128])
 def test_4k_precision_form_sampled(ctx, nb):
     """The benchmark workload at full size and launch configuration, checked on sampled pixels:
     FP32 depth with FP16 normal/radiance, 4 slices, 32 steps, 4 ambient cones."""
@@ -162,16 +165,15 @@ def test_invalid_arguments_enqueue_nothing(ctx):
     r = torch.from_numpy(g.radiance).cuda()
     out0 = torch.full((32, 32, 4), 5.0, device="cuda")
     bad = [Params(num_slices=0), Params(num_slices=17), Params(steps_per_side=65), Params(radius=-1.0),
-           Params(thickness=0.0), Params(sector_count=48), Params(hit_rule=2), Params(ambient_cones=3)]
+           Params(thickness=0.0), Params(sector_count=48), Params(sector_count=96), Params(hit_rule=2),
+           Params(ambient_cones=3)]
     for prm in bad:
         with pytest.raises(ssilvb.SsilvbError) as ei:
             ctx.gather(d, n, r, g.camera, prm, out0, None, None)
         assert ei.value.code == 1
     with pytest.raises(ssilvb.SsilvbError) as ei:
-        ctx.gather(d, n, r, g.camera, Params(sector_count=128), out0, None, None)
-    assert ei.value.code == 2
-    with pytest.raises(ssilvb.SsilvbError):
         ctx.gather(d, n.half(), r, g.camera, Params(), out0, None, None)
+    assert ei.value.code == 2
     # a host pointer where device memory is required
     with pytest.raises(ssilvb.SsilvbError):
         ctx.gather(torch.from_numpy(g.depth), n, r, g.camera, Params(), out0, None, None)

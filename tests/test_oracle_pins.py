@@ -34,23 +34,23 @@ def _read_cases():
 
 @pytest.mark.parametrize("nb,rule,A,B,expect", _read_cases())
 def test_hit_rule_hand_cases(nb, rule, A, B, expect):
-    assert oracle.sector_mask64(A, B, nb, rule) == expect
-    assert oracle.sector_mask32(A, B, nb, rule) == expect
+    assert oracle.sector_mask_words(A, B, nb, rule, fp64=True) == expect
+    assert oracle.sector_mask_words(A, B, nb, rule) == expect
 
 
-@pytest.mark.parametrize("nb", [32, 64])
+@pytest.mark.parametrize("nb", [32, 64, 128])
 @pytest.mark.parametrize("rule", [0, 1])
 def test_hit_rule_o1_equals_per_sector(nb, rule):
     """The O(1) run of ones equals the per-sector brute force on a grid of exact endpoints,
     including every tie (endpoints on sector centres and widths of exactly 1/2)."""
-    step = 1.0 / 8.0 if nb == 32 else 1.0 / 4.0
+    step = {32: 1.0 / 8.0, 64: 1.0 / 4.0, 128: 1.0 / 2.0}[nb]
     vals = np.arange(0.0, nb + step / 2, step)
     fine = np.arange(0.0, 2.5, 1.0 / 128.0)
     for grid in (vals, fine):
         for A in grid:
             for B in grid[grid >= A]:
                 a, b = float(A), float(B)
-                assert oracle.sector_mask32(a, b, nb, rule) == oracle.sector_mask64(a, b, nb, rule), (a, b)
+                assert oracle.sector_mask_words(a, b, nb, rule) == oracle.sector_mask_words(a, b, nb, rule, True), (a, b)
 
 
 def test_hit_rule_random_endpoints():
@@ -123,7 +123,7 @@ def _horizon_masks(g, nd, ns, radius, nb):
     half-covered rule; restated here in FP64 from the definition."""
     H, W = g.depth.shape
     cam = g.camera
-    out = np.zeros((H * W, nd), dtype=np.uint64)
+    out = np.zeros((H * W, nd), dtype=object if nb == 128 else np.uint64)
     for y in range(H):
         for x in range(W):
             z = float(g.depth[y, x])
@@ -149,13 +149,16 @@ def _horizon_masks(g, nd, ns, radius, nb):
     return out
 
 
-@pytest.mark.parametrize("nb", [32, 64])
+@pytest.mark.parametrize("nb", [32, 64, 128])
 def test_infinite_thickness_equals_quantised_horizon(nb):
     g = scenegen.render(11, 28, 22, 6, 2)
     prm = Params(num_slices=2, steps_per_side=6, radius=3.0, thickness=INF, sector_count=nb)
     _, _, masks, margin = oracle.fp64(oracle.Problem(g, prm, None))
     ref = _horizon_masks(g, 2, 6, 3.0, nb)
     assert np.count_nonzero(ref) > 20
+    if nb == 128:
+        masks = masks[..., 0].astype(object) | (masks[..., 1].astype(object) << 64)
+        ref = ref.astype(object)
     diff = masks != ref
     assert np.all(margin[diff] < 1e-9)
     assert diff.mean() < 1e-3
