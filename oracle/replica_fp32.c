@@ -32,8 +32,27 @@
 
 #include "oracle.h"
 
-#define RSQRT_OPS 13
-#define ACOS_OPS 13
+/* Algorithmic op counts per block: one per IEEE add/sub/mul/fma/div/sqrt, compare, select,
+ * min/max, conversion, shift, logic op and popcount the code below performs (memory loads and
+ * stores are not ops).  W = 64-bit words of the mask (2 for 128 sectors, else 1). */
+#define RSQRT_OPS 13          /* max, shift, subtract, half, 3 x (square, fma, multiply) */
+#define ACOS_OPS 13           /* 1 - a, max, sqrt, 7 fma, multiply, compare, select */
+#define OPS_STEP_HEAD 12      /* loop compare + increment, j+1 and its conversion, offset fma,
+                                 two roundings (fma, subtract), centre test (2 compares, and) */
+#define OPS_STEP_QUAD 2       /* quadratic steps: square and scale */
+#define OPS_STEP_PIXEL 11     /* two conversions, two adds, bounds test (4 compares, 3 ors) */
+#define OPS_STEP_DEPTH 5      /* index multiply-add, geometry test (2 compares, and) */
+#define OPS_FRONT_COS 14      /* sample ray 2, l 3, l.v 3, |l|^2 3, edge-band test 3 */
+#define OPS_FRONT_ANGLE (RSQRT_OPS + 1 + ACOS_OPS + 3 + 1) /* rsqrt, cosine, acos, map + clamp, band test */
+#define OPS_BACK (3 + RSQRT_OPS + 1 + ACOS_OPS + 3)        /* l_b.v, |l_b|^2, rsqrt, cosine, acos, map */
+#define OPS_RUN(W) (2 + 17 + 4 * ((W) - 1) + ((W) == 1 ? 3 : 7) + (W) + 2)
+                              /* endpoint selects 2; run: width test 2, ceil/floor path 6,
+                                 empty test 1, two low-bit masks 6, and-not 2 (per extra word +4);
+                                 newly: not, and, popcount (two words: 7); or; GI test 2 */
+#define OPS_GI 17             /* two clamped cosines 10, weight 4, three fma */
+#define OPS_CONE(W) (11 + 4 * ((W) - 1) + 4 + 6 + 9 + 15 + 2 + 27 + 3 + 2)
+                              /* group mask and count 11, direction 10, world 9, SH basis 15,
+                                 weight 2, three 9-term sums 27, accumulate 3, loop 2 */
 
 /* Abramowitz and Stegun 4.4.46 coefficients a0..a7. */
 static const float AS0 = 1.5707963050f, AS1 = -0.2145988016f, AS2 = 0.0889789874f, AS3 = -0.0501743046f;
@@ -128,6 +147,7 @@ int orc32_pixels(const orc_problem *pb, int n, const int32_t *xy, float *out0, f
     const int nb = pb->sector_count, na = pb->ambient_cones;
     const int words = nb == 128 ? 2 : 1;
     const int inf_t = isinf(pb->thickness);
+    const int ops_run = OPS_RUN(words), ops_cone = OPS_CONE(words);
     int64_t c_pix = 0, c_sky = 0, c_slice = 0, c_visit = 0, c_skip = 0, c_gi = 0, ops = 0;
 
     /* Per-launch constants, binary32 unless noted. */
@@ -239,7 +259,8 @@ int orc32_pixels(const orc_problem *pb, int n, const int32_t *xy, float *out0, f
             const float cu_m = fmaf(cg, cdel, -(sg * sdel)), su_m = fmaf(sg, cdel, cg * sdel);
             const float thr_p = cu_p >= 0.0f ? -su_p : (su_p < 0.0f ? 2.0f : -2.0f);
             const float thr_m = cu_m >= 0.0f ? su_m : (su_m > 0.0f ? 2.0f : -2.0f);
-            const float thr2_p = thr_p * thr_p, thr2_m = thr_m * thr_m;
+            /* signed squares: the test "cosine below thr" is dv |dv| < thr |thr| |l|^2 */
+            const float thr2_p = thr_p * fabsf(thr_p), thr2_m = thr_m * fabsf(thr_m);
             ops += 2 + 2 + 3 + 3 + RSQRT_OPS + 3 + 6 + 2 + 1 + 1 + 2 + 8 + 8 + 2;
 
             mask_t b = 0;
@@ -248,7 +269,7 @@ int orc32_pixels(const orc_problem *pb, int n, const int32_t *xy, float *out0, f
                 const float wsx = pos ? cphi : -cphi, wsy = pos ? sphi : -sphi;
                 const float sK = pos ? K : -K;
                 const float edge = pos ? f_nb : 0.0f;
-                const float thr = pos ? thr_p : thr_m, thr2 = pos ? thr2_p : thr2_m;
+                const float thr2 = pos ? thr2_p : thr2_m;
                 for (int j = 0; j < ns; ++j) {
                     ++c_visit;
                     /* Step offset along the direction and the nearest pixel (ties to even). */
@@ -262,14 +283,14 @@ int orc32_pixels(const orc_problem *pb, int n, const int32_t *xy, float *out0, f
                     /* nearest integer (ties to even) of the exact product, via a fused add of 1.5*2^23 */
                     const float dxf = fmaf(o, wsx, 12582912.0f) - 12582912.0f;
                     const float dyf = fmaf(o, wsy, 12582912.0f) - 12582912.0f;
-                    ops += 1 + 2 * (pb->step_mode != 0) + 4 + 3;
+                    ops += OPS_STEP_HEAD + OPS_STEP_QUAD * (pb->step_mode != 0);
                     if (dxf == 0.0f && dyf == 0.0f) { ++c_skip; continue; }
                     const int qx = x + (int)dxf, qy = y + (int)dyf;
-                    ops += 4 + 3;
+                    ops += OPS_STEP_PIXEL;
                     if (qx < 0 || qy < 0 || qx >= W || qy >= H) { ++c_skip; continue; }
                     const size_t q = (size_t)qy * W + qx;
                     const float zq = pb->depth[q];
-                    ops += 2 + 3;
+                    ops += OPS_STEP_DEPTH;
                     if (!is_geometry(zq)) { ++c_skip; continue; }
 
                     /* Front sample: l = s_f - p, its cosine to v, its sector coordinate.  The sample's
@@ -278,19 +299,16 @@ int orc32_pixels(const orc_problem *pb, int n, const int32_t *xy, float *out0, f
                     const float lx = fmaf(aq, zq, -px), ly = fmaf(bq, zq, -py), lz = z - zq;
                     const float dv = fmaf(lx, vx, fmaf(ly, vy, lz * vz));
                     const float ll = fmaf(lx, lx, fmaf(ly, ly, lz * lz));
-                    ops += 2 + 3 + 6 + 6;
-                    /* Inside the edge band (cosine test on dv / sqrt(ll) against thr without the
-                     * square root): by the half-covered rule (Section 3.1) the sample occludes
-                     * nothing, because its back endpoint lies still closer to that edge. */
-                    {
-                        const float d2 = dv * dv, r2 = thr2 * ll;
-                        const int beyond = thr >= 0.0f ? (dv < 0.0f || d2 < r2) : (dv < 0.0f && d2 > r2);
-                        if (beyond) continue;
-                    }
+                    ops += OPS_FRONT_COS;
+                    /* Inside the edge band (cosine dv / sqrt(ll) below thr, compared through the
+                     * monotone map x -> x |x| without the square root): by the half-covered rule
+                     * (Section 3.1) the sample occludes nothing, because its back endpoint lies
+                     * still closer to that edge. */
+                    if (dv * fabsf(dv) < thr2 * ll) continue;
                     const float rl = orc32_rsqrt(ll);
                     const float cf = dv * rl;
                     const float Xf = fminf(fmaxf(fmaf(orc32_acos(cf), sK, off), 0.0f), f_nb);
-                    ops += RSQRT_OPS + 1 + ACOS_OPS + 3 + 1;
+                    ops += OPS_FRONT_ANGLE;
                     /* The same band in sector units (exact for the computed endpoint). */
                     if (pos ? Xf > edge_hi : Xf < edge_lo) continue;
 
@@ -303,7 +321,7 @@ int orc32_pixels(const orc_problem *pb, int n, const int32_t *xy, float *out0, f
                         const float llb = fmaf(m2t, dv, ll + t2);
                         const float cb = dvb * orc32_rsqrt(llb);
                         Xb = fminf(fmaxf(fmaf(orc32_acos(cb), sK, off), 0.0f), f_nb);
-                        ops += 3 + RSQRT_OPS + 1 + ACOS_OPS + 3;
+                        ops += OPS_BACK;
                     }
                     /* The back endpoint lies toward this side's edge: [A, B] = [X_f, X_b] on side +,
                      * [X_b, X_f] on side - (a rounding-level reversal leaves B < A: no sector). */
@@ -311,7 +329,7 @@ int orc32_pixels(const orc_problem *pb, int n, const int32_t *xy, float *out0, f
                     const mask_t bj = sector_run(A, B, nb, pb->hit_rule);
                     const int newly = popc128(bj & ~b);
                     b |= bj;
-                    ops += 12 + 3 + 1;
+                    ops += ops_run;
 
                     /* Indirect light from the newly occluded sectors (Section 3.3). */
                     if (newly > 0 && pb->gi) {
@@ -323,7 +341,7 @@ int orc32_pixels(const orc_problem *pb, int n, const int32_t *xy, float *out0, f
                         GIr = fmaf(wgt, cj[0], GIr);
                         GIg = fmaf(wgt, cj[1], GIg);
                         GIb = fmaf(wgt, cj[2], GIb);
-                        ops += 5 + 5 + 4 + 3;
+                        ops += OPS_GI;
                     }
                 }
             }
@@ -363,7 +381,7 @@ int orc32_pixels(const orc_problem *pb, int n, const int32_t *xy, float *out0, f
                 AMr = fmaf(wt, L[0], AMr);
                 AMg = fmaf(wt, L[1], AMg);
                 AMb = fmaf(wt, L[2], AMb);
-                ops += 3 + 4 + 6 + 9 + 17 + 2 + 27 + 3;
+                ops += ops_cone;
             }
             if (masks) {
                 masks[((size_t)pi * nd + i) * words] = (uint64_t)b;

@@ -265,10 +265,10 @@ __device__ __forceinline__ Step make_step(const GatherParams &P, const Pixel &X,
 
 
 // One sample of side POS (+omega when true): front and back endpoints, sector run, mask
-// update and indirect light.  thr/thr2: the side's edge-band cosine threshold and its square.
+// update and indirect light.  thr2: the side's edge-band cosine threshold times its magnitude.
 template <int NB, bool F16, bool INF_T, bool POS>
 __device__ __forceinline__ void process_step(const GatherParams &P, const Pixel &X, const Step &s, float off,
-                                             float thr, float thr2, typename MaskT<NB>::T &b, float &GIr,
+                                             float thr2, typename MaskT<NB>::T &b, float &GIr,
                                              float &GIg, float &GIb) {
     using M = typename MaskT<NB>::T;
     const float zq = s.zq;
@@ -278,13 +278,10 @@ __device__ __forceinline__ void process_step(const GatherParams &P, const Pixel 
     const float lx = fmaf(aq, zq, -X.px), ly = fmaf(bq, zq, -X.py), lz = X.z - zq;
     const float dv = fmaf(lx, X.vx, fmaf(ly, X.vy, lz * X.vz));
     const float ll = fmaf(lx, lx, fmaf(ly, ly, lz * lz));
-    // Inside this side's edge band (cosine dv/|l| below thr, tested without the square root):
-    // the back endpoint lies still closer to the edge, so no sector is half covered.
-    {
-        const float d2 = dv * dv, r2 = thr2 * ll;
-        const bool beyond = thr >= 0.0f ? (dv < 0.0f || d2 < r2) : (dv < 0.0f && d2 > r2);
-        if (beyond) return;
-    }
+    // Inside this side's edge band (cosine dv/|l| below thr, compared as dv |dv| < thr |thr| |l|^2
+    // through the monotone map x -> x |x|): the back endpoint lies still closer to the edge, so
+    // no sector is half covered.
+    if (dv * fabsf(dv) < thr2 * ll) return;
     const float sK = POS ? P.K : -P.K;
     const float rl = own_rsqrt(ll);
     const float Xf = fminf(fmaxf(fmaf(own_acos(dv * rl), sK, off), 0.0f), P.f_nb);
@@ -321,14 +318,15 @@ __device__ __forceinline__ void process_step(const GatherParams &P, const Pixel 
 // does too (the rounded offset is monotone in j), so the side ends there.
 template <int NB, bool F16, bool INF_T, int STEP_MODE, bool POS>
 __device__ __forceinline__ void march_side(const GatherParams &P, const Pixel &X, int x, int y, float cphi,
-                                           float sphi, float off, float thr, float thr2,
+                                           float sphi, float off, float thr2,
                                            typename MaskT<NB>::T &b, float &GIr, float &GIg, float &GIb) {
     const float wsx = POS ? cphi : -cphi, wsy = POS ? sphi : -sphi;
 #pragma unroll 2
     for (int j = 0; j < P.ns; ++j) {
         const Step st = make_step<STEP_MODE>(P, X, x, y, (float)(j + 1), wsx, wsy);
         if (!st.on) break;
-        if (st.ok && is_geometry(st.zq)) process_step<NB, F16, INF_T, POS>(P, X, st, off, thr, thr2, b, GIr, GIg, GIb);
+        // off-screen and centre steps load depth 0, which is not geometry
+        if (is_geometry(st.zq)) process_step<NB, F16, INF_T, POS>(P, X, st, off, thr2, b, GIr, GIg, GIb);
     }
 }
 
@@ -410,9 +408,9 @@ __device__ __forceinline__ void gather_pixel(const GatherParams &P, int x, int y
 
         M b = 0;
         // Side -omega, then side +omega (Section 3.3: nearer samples occlude later ones first).
-        march_side<NB, F16, INF_T, STEP_MODE, false>(P, X, x, y, cphi, sphi, off, thr_m, thr_m * thr_m, b,
+        march_side<NB, F16, INF_T, STEP_MODE, false>(P, X, x, y, cphi, sphi, off, thr_m * fabsf(thr_m), b,
                                                      GIr, GIg, GIb);
-        march_side<NB, F16, INF_T, STEP_MODE, true>(P, X, x, y, cphi, sphi, off, thr_p, thr_p * thr_p, b,
+        march_side<NB, F16, INF_T, STEP_MODE, true>(P, X, x, y, cphi, sphi, off, thr_p * fabsf(thr_p), b,
                                                     GIr, GIg, GIb);
 
         // Slice end: unoccluded fraction, then the ambient cones (Section 3.2).
