@@ -55,6 +55,30 @@ def make_workload(name, nb):
     return scenegen.workload_256()
 
 
+def kernel_sources_sha256():
+    """Hash of the CUDA sources and the ABI header: measured counters apply only to this code."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2301_11376_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)) + ["../../include/ssilvb.h"]:
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + b"\0" + fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(key):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the ncu capture
+    recorded in profiles/traffic.json, or None when the kernel sources changed since."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f).get(key)
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("sources_sha256") != kernel_sources_sha256():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
 def samples_per_frame(w):
     H, W = w.gbuf.depth.shape
     return H * W * 2 * w.params.num_slices * w.params.steps_per_side
@@ -504,8 +528,10 @@ def main():
     peak_ops = SM_COUNT_GB300 * FP32_LANES_PER_SM * 2.070e9
     achieved = ops / (ms / 1e3)
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
-            "frac": achieved / peak_ops, "traffic": None,
-            "kernel": "gather_tile_kernel", "ops_per_launch": ops,
+            "frac": achieved / peak_ops, "traffic": measured_traffic(f"{args.workload} nb{args.nb}"),
+            "traffic_unit": "bytes per launch (ncu dram read + write)",
+            "algorithmic_bytes": int(H * W * (4 + 2 * g.normal.dtype.itemsize * 4 + 16 + (16 if out1 is not None else 0))),
+            "kernel": "gather_class_kernel", "ops_per_launch": ops,
             "ops_per_sample": ops / spf,
             "peak_note": "152 SMs x 128 FP32 lanes x 2.070 GHz max SM clock (derived)"}
     cpu = None if args.no_cpu_baseline else cpu_baseline(w)
