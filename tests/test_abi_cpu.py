@@ -43,12 +43,31 @@ def test_status_strings(lib):
     assert lib.ssilvb_version() >= 10000
 
 
-def test_struct_layouts_match_header():
-    # sizes of the ctypes mirrors on this ABI (LP64): checked against the C declarations
-    assert ctypes.sizeof(ssilvb.Gbuffer) == 8 + 8 * 2 + (8 + 8 + 8) * 2 + 16
-    assert ctypes.sizeof(ssilvb.CameraC) == 13 * 4
-    assert ctypes.sizeof(ssilvb.ParamsC) == 4 * 10 + 16 + 8
-    assert ctypes.sizeof(ssilvb.Output) == 7 * 8
+def test_struct_layouts_match_header(tmp_path):
+    """Every ctypes mirror has the size and field offsets the C compiler gives the header."""
+    import subprocess
+    mirrors = {"ssilvb_gbuffer": ssilvb.Gbuffer, "ssilvb_camera": ssilvb.CameraC, "ssilvb_params": ssilvb.ParamsC,
+               "ssilvb_output": ssilvb.Output, "ssilvb_tuning": ssilvb.Tuning, "ssilvb_frame": ssilvb.Frame}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "ssilvb.h"', "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", ssilvb.INCLUDE, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            parts = line.split()
+            got[(parts[0], parts[1])] = int(parts[2])
+    for cname, py in mirrors.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
 
 
 def test_null_arguments_rejected_without_gpu(lib):

@@ -179,3 +179,14 @@ def test_invalid_arguments_enqueue_nothing(ctx):
         ctx.gather(torch.from_numpy(g.depth), n, r, g.camera, Params(), out0, None, None)
     torch.cuda.synchronize()
     assert torch.all(out0 == 5.0)
+
+
+@pytest.mark.parametrize("frame", [1, 7, 63])
+def test_temporal_noise_frames(ctx, frame):
+    """Per-frame noise rotation (Section 3.1: the integral is distributed spatially and
+    temporally): each frame's table is an input like any other and the gather stays exact."""
+    g = scenegen.render(30 + frame, 72, 56, 10, 3)
+    prm = Params(num_slices=2, steps_per_side=10, step_mode=1)
+    noise = scenegen.ign_table(frame)
+    res = run_gpu(ctx, g, prm, noise)
+    check_parity(g, prm, noise, None, res)

@@ -322,3 +322,15 @@ def test_replica_vs_fp64_on_256():
     assert np.all(margin[diff] < 1e-3)
     assert same.mean() > 0.99
     assert np.abs(r0[same] - o0[same]).max() < 1e-5
+
+
+def test_temporal_noise_tables_vary_and_stay_in_range():
+    base = scenegen.ign_table(0)
+    seen = set()
+    for f in range(8):
+        t = scenegen.ign_table(f)
+        assert t.shape == (16, 2) and np.all(t >= 0.0) and np.all(t < 1.0)
+        # xi_s = frac(xi_phi + 1/2)
+        np.testing.assert_allclose((t[:, 0].astype(np.float64) + 0.5) % 1.0, t[:, 1], atol=1e-6)
+        seen.add(t.tobytes())
+    assert len(seen) == 8 and np.array_equal(base, scenegen.ign_table(64))
