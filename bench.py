@@ -39,7 +39,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ssilvb", choices=["ssilvb", "reference"])
-    ap.add_argument("--workload", default="4k", choices=["4k", "1080p", "256", "batch", "serve", "trends"])
+    ap.add_argument("--workload", default="4k",
+                    choices=["4k", "1080p", "256", "batch", "serve", "trends", "precision"])
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--nb", type=int, default=32)
     ap.add_argument("--no-e2e", action="store_true")
@@ -383,6 +384,61 @@ def run_trend_sweep(args, world, rank, local):
     print(json.dumps(out))
 
 
+def run_precision_study(args, world, rank, local):
+    """FP16 storage of normals and radiance (FP32 depth, FP32 arithmetic) at 4K: error per
+    output (1) against the FP64 oracle on the same FP16 inputs (arithmetic error, the gated
+    one) and (2) against the FP64 oracle on the FP32 G-buffer (storage error, reported), on a
+    uniform pixel sample; bitmask agreement with the binary32 replica on the same sample."""
+    import torch
+
+    import oracle
+    import paper_2301_11376_gb300 as ssilvb
+    ssilvb.build()
+    if rank != 0:
+        return
+    dev = torch.device("cuda", local)
+    ctx = ssilvb.Context(local)
+    g32 = scenegen.render(3, 3840, 2160, 64, 16)
+    g16 = g32.as_f16()
+    noise, sh = scenegen.ign_table(), scenegen.sh_environment(7)
+    H, W = g32.depth.shape
+    rng = np.random.default_rng(17)
+    idx = rng.choice(H * W, 12000, replace=False)
+    xy = np.stack([idx % W, idx // W], 1).astype(np.int32)
+    rows = []
+    for nb in (32, 64, 128):
+        prm = scenegen.Params(4, 32, 2.0, 0.5, sector_count=nb, ambient_cones=4)
+        res = {}
+        for name, g in (("f16", g16), ("f32", g32)):
+            d = torch.from_numpy(g.depth).to(dev)
+            n = torch.from_numpy(np.ascontiguousarray(g.normal)).to(dev)
+            r = torch.from_numpy(np.ascontiguousarray(g.radiance)).to(dev)
+            o0, o1, m = ssilvb.alloc_outputs(H, W, prm, dev, masks=True)
+            ctx.gather(d, n, r, g.camera, prm, o0, o1, m, noise=noise, sh=sh)
+            torch.cuda.synchronize()
+            res[name] = (o0.cpu().numpy().reshape(-1, 4)[idx].astype(np.float64),
+                         o1.cpu().numpy().reshape(-1, 4)[idx].astype(np.float64))
+        e16 = oracle.fp64(oracle.Problem(g16, prm, noise, sh), xy)
+        e32 = oracle.fp64(oracle.Problem(g32, prm, noise, sh), xy)
+
+        def stats(a, b):
+            err = np.abs(a - b)
+            return {"max": float(err.max()), "p99": float(np.percentile(err, 99)), "mean": float(err.mean())}
+        g0, g1 = res["f16"]
+        rows.append({"sector_count": nb,
+                     "arithmetic_vs_fp64_same_fp16_inputs": {"AO": stats(g0[:, 3], e16[0][:, 3]),
+                                                             "GI": stats(g0[:, :3], e16[0][:, :3]),
+                                                             "ambient": stats(g1[:, :3], e16[1][:, :3])},
+                     "storage_vs_fp64_on_fp32_gbuffer": {"AO": stats(g0[:, 3], e32[0][:, 3]),
+                                                         "GI": stats(g0[:, :3], e32[0][:, :3]),
+                                                         "ambient": stats(g1[:, :3], e32[1][:, :3])},
+                     "fp32_storage_vs_fp64": {"AO": stats(res["f32"][0][:, 3], e32[0][:, 3]),
+                                              "GI": stats(res["f32"][0][:, :3], e32[0][:, :3])},
+                     "pixels": len(idx)})
+    print(json.dumps({"metric": "precision study (abs error per output)", "workload": "3840x2160 seed 3, "
+                      "N_d 4, N_s 32, 4 cones, FP16 normal+radiance vs FP32", "rows": rows}))
+
+
 def run_serve_bench(args, world, rank, local):
     """Poisson stream (mean 2000 req/s) of frames 720p..4K, N_d 1-8, N_b 32/64, N_s 8/16/32, on
     resident G-buffers (2 seeds per size): continuous-batching server vs one launch + host sync
@@ -450,6 +506,9 @@ def main():
         return
     if args.workload == "trends":
         run_trend_sweep(args, world, rank, local)
+        return
+    if args.workload == "precision":
+        run_precision_study(args, world, rank, local)
         return
     import torch
 
