@@ -593,6 +593,16 @@ def main():
             "kernel": "gather_class_kernel", "ops_per_launch": ops,
             "ops_per_sample": ops / spf,
             "peak_note": "152 SMs x 128 FP32 lanes x 2.070 GHz max SM clock (derived)"}
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except (OSError, ValueError):
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    alg_gbs = roof["algorithmic_bytes"] / (ms / 1e3) / 1e9
+    roof["hbm_context"] = {"algorithmic_GBps": alg_gbs, "peak_GBps": hbm_peak, "frac": alg_gbs / hbm_peak,
+                           "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
     cpu = None if args.no_cpu_baseline else cpu_baseline(w)
     out = {"metric": "Gsamples/s (ms/frame at 4K)", "value": value, "unit": "Gsamples/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,

@@ -283,7 +283,6 @@ class Context:
             st = a.stride(0) * a.element_size() if hasattr(a, "element_size") else a.strides[0]
             return st
 
-        import numpy as np
         nfmt = FMT_F16X4 if (str(normal.dtype).endswith("float16")) else FMT_F32X4
         rfmt = FMT_F16X4 if (str(radiance.dtype).endswith("float16")) else FMT_F32X4
         H, W = depth.shape[:2]
@@ -296,7 +295,6 @@ class Context:
         sh_ = stream.cuda_stream if stream is not None else None
         self._check(self.lib.ssilvb_gather_host(self.handle, ctypes.byref(g), ctypes.byref(_camera_c(camera)),
                                                 ctypes.byref(pc), ctypes.byref(o), ctypes.c_void_p(sh_)))
-        del np
 
     def frame(self, depth, normal, radiance, camera, params, out0, out1=None, masks=None, noise=None, sh=None,
               keep=None):

@@ -177,6 +177,14 @@ def test_invalid_arguments_enqueue_nothing(ctx):
     # a host pointer where device memory is required
     with pytest.raises(ssilvb.SsilvbError):
         ctx.gather(torch.from_numpy(g.depth), n, r, g.camera, Params(), out0, None, None)
+    # misaligned planes and pitches
+    big = torch.zeros(32 * 33 + 1, device="cuda")
+    with pytest.raises(ssilvb.SsilvbError) as ei:
+        ctx.gather(big[1:32 * 32 + 1].view(32, 32), n, r, g.camera, Params(), out0, None, None)
+    assert ei.value.code == 1
+    wide = torch.zeros((32, 36, 4), device="cuda")
+    with pytest.raises(ssilvb.SsilvbError):  # out0 rows shorter than the image
+        ctx.gather(d, n, r, g.camera, Params(), wide[:, :30], None, None)
     torch.cuda.synchronize()
     assert torch.all(out0 == 5.0)
 
