@@ -182,9 +182,10 @@ def test_invalid_arguments_enqueue_nothing(ctx):
     with pytest.raises(ssilvb.SsilvbError) as ei:
         ctx.gather(big[1:32 * 32 + 1].view(32, 32), n, r, g.camera, Params(), out0, None, None)
     assert ei.value.code == 1
-    wide = torch.zeros((32, 36, 4), device="cuda")
-    with pytest.raises(ssilvb.SsilvbError):  # out0 rows shorter than the image
-        ctx.gather(d, n, r, g.camera, Params(), wide[:, :30], None, None)
+    short = torch.zeros(32 * 30 * 4 + 8 * 4, device="cuda").as_strided((32, 32, 4), (30 * 4, 4, 1))
+    with pytest.raises(ssilvb.SsilvbError) as ei:  # out0 pitch shorter than a row of the image
+        ctx.gather(d, n, r, g.camera, Params(), short, None, None)
+    assert ei.value.code == 1
     torch.cuda.synchronize()
     assert torch.all(out0 == 5.0)
 
