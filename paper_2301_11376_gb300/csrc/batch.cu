@@ -308,7 +308,7 @@ ssilvb_status ssilvb_autotune(ssilvb_ctx *ctx, const ssilvb_frame *frames, int n
     if (e0 != cudaSuccess) return cuda_fail(ctx, e0, "autotune warm-up");
 
     std::vector<KernelChoice> cands;
-    for (int minb : {8, 10}) {
+    for (int minb : {8, 9}) {
         KernelChoice k;
         k.mapping = SSILVB_MAP_CLASS;
         k.minb = minb;
@@ -354,7 +354,7 @@ ssilvb_status ssilvb_autotune(ssilvb_ctx *ctx, const ssilvb_frame *frames, int n
         KernelChoice best_s;
         float t_best_s = 1e30f;
         for (int mapping : {SSILVB_MAP_CLASS, SSILVB_MAP_TILE})
-            for (int minb : {8, 10}) {
+            for (int minb : {8, 9}) {
                 if (mapping == SSILVB_MAP_TILE && minb == 8) continue;
                 KernelChoice k;
                 k.mapping = mapping;

@@ -68,6 +68,32 @@ struct GatherParams {
     float Y0, Y1, Y2, Y3, Y4;
 };
 
+// Packed binary32 pairs (add/sub/mul/fma.rn.f32x2).  Each half is one IEEE binary32 operation
+// rounded to nearest even with subnormals kept, i.e. exactly the scalar operation, so computing two
+// independent values as a pair changes no result bit and takes one issue slot instead of two.
+#define SSILVB_PAIR_OP3(name, op)                                                                    \
+    __device__ __forceinline__ float2 name(float2 a, float2 b, float2 c) {                         \
+        float2 d;                                                                                  \
+        asm("{.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"      \
+            "mov.b64 rc, {%6, %7};\n\t" op " rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;}"            \
+            : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y)); \
+        return d;                                                                                  \
+    }
+#define SSILVB_PAIR_OP2(name, op)                                                                    \
+    __device__ __forceinline__ float2 name(float2 a, float2 b) {                                   \
+        float2 d;                                                                                  \
+        asm("{.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"          \
+            op " rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;}"                                            \
+            : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));                     \
+        return d;                                                                                  \
+    }
+SSILVB_PAIR_OP3(pfma, "fma.rn.f32x2")
+SSILVB_PAIR_OP2(pmul, "mul.rn.f32x2")
+SSILVB_PAIR_OP2(psub, "sub.rn.f32x2")
+#undef SSILVB_PAIR_OP3
+#undef SSILVB_PAIR_OP2
+__device__ __forceinline__ float2 bcast(float a) { return make_float2(a, a); }
+
 // Abramowitz and Stegun 4.4.46: acos(x) = sqrt(1 - x) (a0 + a1 x + ... + a7 x^7), 0 <= x <= 1.
 __device__ __forceinline__ float own_acos(float c) {
     const float a = fabsf(c);
@@ -96,6 +122,34 @@ __device__ __forceinline__ float own_rsqrt(float x) {
         y = y * u;
     }
     return y;
+}
+
+// own_rsqrt and own_acos of two arguments at once, operation for operation the same.
+__device__ __forceinline__ float2 own_rsqrt_pair(float2 x) {
+    x.x = fmaxf(x.x, 1.17549435e-38f);
+    x.y = fmaxf(x.y, 1.17549435e-38f);
+    float2 y = make_float2(__uint_as_float(0x5f3759dfu - (__float_as_uint(x.x) >> 1)),
+                           __uint_as_float(0x5f3759dfu - (__float_as_uint(x.y) >> 1)));
+    const float2 nhx = pmul(bcast(-0.5f), x);  // -(0.5 x), exactly
+#pragma unroll
+    for (int k = 0; k < 3; ++k) y = pmul(y, pfma(nhx, pmul(y, y), bcast(1.5f)));
+    return y;
+}
+
+__device__ __forceinline__ float2 own_acos_pair(float2 c) {
+    const float2 a = make_float2(fabsf(c.x), fabsf(c.y));
+    const float2 om = psub(bcast(1.0f), a);
+    const float2 s = make_float2(sqrtf(fmaxf(om.x, 0.0f)), sqrtf(fmaxf(om.y, 0.0f)));
+    float2 Q = pfma(bcast(-0.0012624911f), a, bcast(0.0066700901f));
+    Q = pfma(Q, a, bcast(-0.0170881256f));
+    Q = pfma(Q, a, bcast(0.0308918810f));
+    Q = pfma(Q, a, bcast(-0.0501743046f));
+    Q = pfma(Q, a, bcast(0.0889789874f));
+    Q = pfma(Q, a, bcast(-0.2145988016f));
+    Q = pfma(Q, a, bcast(1.5707963050f));
+    const float2 r = pmul(s, Q);
+    return make_float2(c.x < 0.0f ? 3.14159265358979323846f - r.x : r.x,
+                       c.y < 0.0f ? 3.14159265358979323846f - r.y : r.y);
 }
 
 // 1.5 * 2^23: adding it to |v| < 2^22 leaves round(v) in the low mantissa bits.
@@ -212,22 +266,6 @@ __device__ __forceinline__ void write_light(const GatherParams &P, int x, int y,
     }
 }
 
-// Which pixel step j of a side reads (nearest pixel, ties to even, through the 1.5*2^23
-// add), whether it is on screen and not the centre pixel, and its depth (loaded now so
-// that the load overlaps the previous sample's arithmetic).
-struct Step {
-    float dxf, dyf;  // integer pixel offsets as floats
-    int qx, qy;
-    float zq;        // depth at the sample pixel (0 when the step is off-screen or the centre)
-    bool on;         // the sample pixel is on screen
-    bool ok;         // on screen and not the centre pixel
-};
-
-struct Pixel;
-template <int STEP_MODE>
-__device__ __forceinline__ Step make_step(const GatherParams &P, const Pixel &X, int x, int y, float jf, float wsx,
-                                          float wsy);
-
 // Per-pixel state the sample loop reads.
 struct Pixel {
     float z, ax, by, px, py, vx, vy, vz, tp, t2, m2t;
@@ -237,64 +275,33 @@ struct Pixel {
     float3 n;
 };
 
-// Offset of step j (jf = j + 1) along the direction, r (jf + xi_s)/(N_s + 1) or its quadratic
-// form, and its nearest pixel: fma(o, w, 1.5*2^23) rounds o*w to the nearest integer (ties to
-// even) in the low mantissa bits, so qx = bits - (0x4B400000 - x).
-template <int STEP_MODE>
-__device__ __forceinline__ Step make_step(const GatherParams &P, const Pixel &X, int x, int y, float jf, float wsx,
-                                          float wsy) {
-    Step s;
-    float o;
-    if (STEP_MODE == 0) {
-        o = fmaf(jf, X.del, X.xdel);
-    } else {
-        const float uj = fmaf(jf, X.dn_, X.xidn);
-        o = (uj * uj) * X.rpx;
-    }
-    const float rx = fmaf(o, wsx, kMagic), ry = fmaf(o, wsy, kMagic);
-    s.dxf = rx - kMagic;
-    s.dyf = ry - kMagic;
-    s.qx = __float_as_int(rx) + X.qx0;
-    s.qy = __float_as_int(ry) + X.qy0;
-    s.on = (unsigned)s.qx < (unsigned)P.W && (unsigned)s.qy < (unsigned)P.H;
-    s.ok = s.on && ((s.qx != x) | (s.qy != y));
-    s.zq = 0.0f;
-    if (s.ok) s.zq = __ldg(P.depth + (unsigned)s.qy * (unsigned)P.depth_pitch + (unsigned)s.qx);
-    return s;
-}
-
-
-// One sample of side POS (+omega when true): front and back endpoints, sector run, mask
-// update and indirect light.  thr2: the side's edge-band cosine threshold times its magnitude.
+// The rest of one sample of side POS (+omega when true) once its front cosine lies outside the
+// side's edge band: front and back endpoints, sector run, mask update and indirect light.
+// (lx, ly, lz) = l = s_f - p, dv = l.v, ll = |l|^2; (qx, qy) the sample pixel.
 template <int NB, bool F16, bool INF_T, bool POS>
-__device__ __forceinline__ void process_step(const GatherParams &P, const Pixel &X, const Step &s, float off,
-                                             float thr2, typename MaskT<NB>::T &b, float &GIr,
-                                             float &GIg, float &GIb) {
+__device__ __forceinline__ void full_step(const GatherParams &P, const Pixel &X, float lx, float ly, float lz, float dv,
+                                          float ll, int qx, int qy, float off, typename MaskT<NB>::T &b,
+                                          float &GIr, float &GIg, float &GIb) {
     using M = typename MaskT<NB>::T;
-    const float zq = s.zq;
-    // Front sample s_f (view ray of the sample pixel = the centre ray plus the pixel offset over
-    // the focal length), l = s_f - p, its cosine to v.
-    const float aq = fmaf(s.dxf, P.inv_fx, X.ax), bq = fmaf(s.dyf, P.ninv_fy, X.by);
-    const float lx = fmaf(aq, zq, -X.px), ly = fmaf(bq, zq, -X.py), lz = X.z - zq;
-    const float dv = fmaf(lx, X.vx, fmaf(ly, X.vy, lz * X.vz));
-    const float ll = fmaf(lx, lx, fmaf(ly, ly, lz * lz));
-    // Inside this side's edge band (cosine dv/|l| below thr, compared as dv |dv| < thr |thr| |l|^2
-    // through the monotone map x -> x |x|): the back endpoint lies still closer to the edge, so
-    // no sector is half covered.
-    if (dv * fabsf(dv) < thr2 * ll) return;
     const float sK = POS ? P.K : -P.K;
-    const float rl = own_rsqrt(ll);
-    const float Xf = fminf(fmaxf(fmaf(own_acos(dv * rl), sK, off), 0.0f), P.f_nb);
-    // the same band in sector units (half a sector for the half-covered rule, the edge for floor/ceil)
-    if (POS ? Xf > P.edge_hi : Xf < P.edge_lo) return;
-    // Back sample, thickness t behind the front one along the centre pixel's view ray.
-    float Xb;
-    if (INF_T) {
-        Xb = POS ? P.f_nb : 0.0f;
-    } else {
+    float rl, Xf, Xb;
+    if (!INF_T) {
+        // Back sample, thickness t behind the front one along the centre pixel's view ray; both
+        // endpoint angles as one pair (a sample outside the cosine band almost always needs both).
         const float dvb = dv - X.tp;
         const float llb = fmaf(X.m2t, dv, ll + X.t2);
-        Xb = fminf(fmaxf(fmaf(own_acos(dvb * own_rsqrt(llb)), sK, off), 0.0f), P.f_nb);
+        const float2 r2 = own_rsqrt_pair(make_float2(ll, llb));
+        rl = r2.x;
+        const float2 e2 = pfma(own_acos_pair(pmul(make_float2(dv, dvb), r2)), bcast(sK), bcast(off));
+        Xf = fminf(fmaxf(e2.x, 0.0f), P.f_nb);
+        // the same band in sector units (half a sector for the half-covered rule, the edge for floor/ceil)
+        if (POS ? Xf > P.edge_hi : Xf < P.edge_lo) return;
+        Xb = fminf(fmaxf(e2.y, 0.0f), P.f_nb);
+    } else {
+        rl = own_rsqrt(ll);
+        Xf = fminf(fmaxf(fmaf(own_acos(dv * rl), sK, off), 0.0f), P.f_nb);
+        if (POS ? Xf > P.edge_hi : Xf < P.edge_lo) return;
+        Xb = POS ? P.f_nb : 0.0f;
     }
     // [A, B]: the back endpoint lies toward this side's edge (a rounding-level reversal gives B < A).
     const float A = POS ? Xf : Xb, B = POS ? Xb : Xf;
@@ -303,8 +310,8 @@ __device__ __forceinline__ void process_step(const GatherParams &P, const Pixel 
     b |= bj;
     // Indirect light of the newly occluded sectors (Section 3.3).
     if (newly > 0 && P.gi) {
-        const float3 cj = load_xyz<F16>(P.radiance, P.radiance_pitch, s.qx, s.qy);
-        const float3 nj = load_xyz<F16>(P.normal, P.normal_pitch, s.qx, s.qy);
+        const float3 cj = load_xyz<F16>(P.radiance, P.radiance_pitch, qx, qy);
+        const float3 nj = load_xyz<F16>(P.normal, P.normal_pitch, qx, qy);
         const float cp = fmaxf(fmaf(X.n.x, lx, fmaf(X.n.y, ly, X.n.z * lz)) * rl, 0.0f);
         const float cq = fmaxf(-(fmaf(nj.x, lx, fmaf(nj.y, ly, nj.z * lz)) * rl), 0.0f);
         const float wgt = (((float)newly * P.inv_nb) * cp) * cq;
@@ -314,19 +321,57 @@ __device__ __forceinline__ void process_step(const GatherParams &P, const Pixel 
     }
 }
 
-// Steps of one side, near to far.  Once a step leaves the screen every later step of that side
-// does too (the rounded offset is monotone in j), so the side ends there.
+// Steps of one side, near to far, two per iteration.  What every step needs (offset, nearest
+// pixel, depth, l = s_f - p, its cosine to v and |l|^2) is computed for steps j and j + 1 as
+// packed pairs; the rest of each sample then runs for step j before step j + 1, so the bitmask and
+// the indirect light see the samples in the same order as one step at a time.  Once a step leaves
+// the screen every later step of that side does too (the rounded offset is monotone in j), so the
+// side ends there.
 template <int NB, bool F16, bool INF_T, int STEP_MODE, bool POS>
 __device__ __forceinline__ void march_side(const GatherParams &P, const Pixel &X, int x, int y, float cphi,
                                            float sphi, float off, float thr2,
                                            typename MaskT<NB>::T &b, float &GIr, float &GIg, float &GIb) {
     const float wsx = POS ? cphi : -cphi, wsy = POS ? sphi : -sphi;
-#pragma unroll 2
-    for (int j = 0; j < P.ns; ++j) {
-        const Step st = make_step<STEP_MODE>(P, X, x, y, (float)(j + 1), wsx, wsy);
-        if (!st.on) break;
-        // off-screen and centre steps load depth 0, which is not geometry
-        if (is_geometry(st.zq)) process_step<NB, F16, INF_T, POS>(P, X, st, off, thr2, b, GIr, GIg, GIb);
+    for (int j = 0; j < P.ns; j += 2) {
+        // offsets r (j + 1 + xi_s)/(N_s + 1), or the quadratic form, of steps j and j + 1
+        const float2 jf = make_float2((float)(j + 1), (float)(j + 2));
+        float2 o;
+        if (STEP_MODE == 0) {
+            o = pfma(jf, bcast(X.del), bcast(X.xdel));
+        } else {
+            const float2 uj = pfma(jf, bcast(X.dn_), bcast(X.xidn));
+            o = pmul(pmul(uj, uj), bcast(X.rpx));
+        }
+        // nearest pixels: fma(o, w, 1.5*2^23) rounds o*w to an integer (ties to even) in the low
+        // mantissa bits, so q = bits - (0x4B400000 - x)
+        const float2 rx = pfma(o, bcast(wsx), bcast(kMagic)), ry = pfma(o, bcast(wsy), bcast(kMagic));
+        const int qxa = __float_as_int(rx.x) + X.qx0, qya = __float_as_int(ry.x) + X.qy0;
+        if (!((unsigned)qxa < (unsigned)P.W && (unsigned)qya < (unsigned)P.H)) break;
+        const int qxb = __float_as_int(rx.y) + X.qx0, qyb = __float_as_int(ry.y) + X.qy0;
+        const bool onb = j + 1 < P.ns && (unsigned)qxb < (unsigned)P.W && (unsigned)qyb < (unsigned)P.H;
+        // depths; 0 (not geometry) for the centre pixel and for a step past the screen or past N_s
+        float za = 0.0f, zb = 0.0f;
+        if ((qxa != x) | (qya != y)) za = __ldg(P.depth + (unsigned)qya * (unsigned)P.depth_pitch + (unsigned)qxa);
+        if (onb && ((qxb != x) | (qyb != y)))
+            zb = __ldg(P.depth + (unsigned)qyb * (unsigned)P.depth_pitch + (unsigned)qxb);
+        // front samples: the view ray of the sample pixel is the centre ray plus the pixel offset
+        // over the focal length; l = s_f - p, its cosine to v and |l|^2
+        const float2 dxf = psub(rx, bcast(kMagic)), dyf = psub(ry, bcast(kMagic));
+        const float2 aq = pfma(dxf, bcast(P.inv_fx), bcast(X.ax)), bq = pfma(dyf, bcast(P.ninv_fy), bcast(X.by));
+        const float2 zq = make_float2(za, zb);
+        const float2 lx = pfma(aq, zq, bcast(-X.px)), ly = pfma(bq, zq, bcast(-X.py));
+        const float2 lz = psub(bcast(X.z), zq);
+        const float2 dv = pfma(lx, bcast(X.vx), pfma(ly, bcast(X.vy), pmul(lz, bcast(X.vz))));
+        const float2 ll = pfma(lx, lx, pfma(ly, ly, pmul(lz, lz)));
+        // Inside this side's edge band (cosine dv/|l| below thr, compared as dv |dv| < thr |thr| |l|^2
+        // through the monotone map x -> x |x|) the back endpoint lies still closer to the edge, so
+        // no sector is half covered.
+        const float2 lim = pmul(bcast(thr2), ll);
+        if (is_geometry(za) && !(dv.x * fabsf(dv.x) < lim.x))
+            full_step<NB, F16, INF_T, POS>(P, X, lx.x, ly.x, lz.x, dv.x, ll.x, qxa, qya, off, b, GIr, GIg, GIb);
+        if (!onb) break;
+        if (is_geometry(zb) && !(dv.y * fabsf(dv.y) < lim.y))
+            full_step<NB, F16, INF_T, POS>(P, X, lx.y, ly.y, lz.y, dv.y, ll.y, qxb, qyb, off, b, GIr, GIg, GIb);
     }
 }
 

@@ -13,7 +13,7 @@ cudaError_t launch_single_t(const GatherParams &P, const KernelChoice &k, cudaSt
     } else {
         dim3 grid((P.W + 127) / 128, P.H);
         if (k.minb == 8) gather_class_kernel<NB, F16, INF_T, SM, 8><<<grid, 128, 0, s>>>(P);
-        else gather_class_kernel<NB, F16, INF_T, SM, 10><<<grid, 128, 0, s>>>(P);
+        else gather_class_kernel<NB, F16, INF_T, SM, 9><<<grid, 128, 0, s>>>(P);
     }
     return cudaGetLastError();
 }
@@ -37,7 +37,7 @@ void single_node_t(const GatherParams &P, const KernelChoice &k, const void **fn
         *block = dim3(256);
     } else {
         *fn = k.minb == 8 ? reinterpret_cast<const void *>(gather_class_kernel<NB, F16, INF_T, SM, 8>)
-                          : reinterpret_cast<const void *>(gather_class_kernel<NB, F16, INF_T, SM, 10>);
+                          : reinterpret_cast<const void *>(gather_class_kernel<NB, F16, INF_T, SM, 9>);
         *grid = dim3((P.W + 127) / 128, P.H);
         *block = dim3(128);
     }
@@ -60,7 +60,7 @@ template <int NB, bool F16, bool INF_T, int SM>
 cudaError_t launch_batch_t(const BatchHeader *hdr, const FrameDesc *frames, unsigned *queue, const KernelChoice &k,
                            int grid, cudaStream_t s) {
     if (k.minb == 8) gather_batch_kernel<NB, F16, INF_T, SM, 8><<<grid, 128, 0, s>>>(hdr, frames, queue);
-    else gather_batch_kernel<NB, F16, INF_T, SM, 10><<<grid, 128, 0, s>>>(hdr, frames, queue);
+    else gather_batch_kernel<NB, F16, INF_T, SM, 9><<<grid, 128, 0, s>>>(hdr, frames, queue);
     return cudaGetLastError();
 }
 
@@ -86,7 +86,7 @@ int batch_occ_t(int minb) {
     int n = 0;
     cudaError_t e = minb == 8
         ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gather_batch_kernel<NB, F16, INF_T, 0, 8>, 128, 0)
-        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gather_batch_kernel<NB, F16, INF_T, 0, 10>, 128, 0);
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gather_batch_kernel<NB, F16, INF_T, 0, 9>, 128, 0);
     return e == cudaSuccess ? n : 0;
 }
 

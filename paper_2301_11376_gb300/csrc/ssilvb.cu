@@ -431,8 +431,8 @@ ssilvb_status ssilvb_set_tuning(ssilvb_ctx *ctx, const ssilvb_tuning *tuning) {
     if (!tuning) return fail(ctx, SSILVB_ERR_INVALID_ARG, "tuning is NULL");
     if (tuning->mapping < SSILVB_MAP_AUTO || tuning->mapping > SSILVB_MAP_CLASS)
         return fail(ctx, SSILVB_ERR_INVALID_ARG, "unknown mapping %d", tuning->mapping);
-    if (tuning->occupancy != 0 && tuning->occupancy != 8 && tuning->occupancy != 10)
-        return fail(ctx, SSILVB_ERR_INVALID_ARG, "occupancy must be 0, 8 or 10");
+    if (tuning->occupancy != 0 && tuning->occupancy != 8 && tuning->occupancy != 9)
+        return fail(ctx, SSILVB_ERR_INVALID_ARG, "occupancy must be 0, 8 or 9");
     if (tuning->rows_per_tile < 0 || tuning->rows_per_tile > 8)
         return fail(ctx, SSILVB_ERR_INVALID_ARG, "rows_per_tile must be 0..8");
     if (tuning->ctas_per_sm < 0 || tuning->ctas_per_sm > 16)

@@ -134,7 +134,7 @@ def test_autotune_keeps_results(ctx):
     import torch
     frames, keep, outs, gbs, prms = _frames(ctx, UNEVEN[:4])
     t = ctx.autotune(frames)
-    assert t.occupancy in (8, 10) and t.rows_per_tile in (1, 2, 4) and t.use_graph in (1, 2)
+    assert t.occupancy in (8, 9) and t.rows_per_tile in (1, 2, 4) and t.use_graph in (1, 2)
     assert t.batch_mode in (1, 2)
     for o in outs:
         o[0].fill_(-3.0)
