@@ -187,9 +187,13 @@ ssilvb_status ssilvb_gather(ssilvb_ctx *ctx, const ssilvb_gbuffer *gbuffer, cons
 
 /* The same gather on HOST buffers: gbuffer and out point to host memory (pinned
  * memory gives the fastest copies).  The context stages the frame in device
- * buffers it owns (grown on demand and kept for reuse), copies the inputs host to
- * device, runs the gather and copies the outputs back, all on stream, and returns
- * after the outputs are in host memory (the call synchronises stream). */
+ * buffers it owns (grown on demand and kept for reuse) and copies the inputs host
+ * to device on stream.  A frame of 512 rows or more then runs as up to 8 row bands,
+ * alternating between stream and a second stream the context owns, and each band's
+ * outputs are copied back on a third context stream while later bands compute.
+ * The results equal one ssilvb_gather launch bit for bit.  The call returns after
+ * the outputs are in host memory, with stream ordered after all of this work (the
+ * call synchronises stream). */
 ssilvb_status ssilvb_gather_host(ssilvb_ctx *ctx, const ssilvb_gbuffer *gbuffer, const ssilvb_camera *camera,
                                  const ssilvb_params *params, const ssilvb_output *out,
                                  struct CUstream_st *stream);

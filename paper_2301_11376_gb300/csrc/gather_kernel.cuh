@@ -51,6 +51,7 @@ struct GatherParams {
     size_t out0_pitch;     // elements (floats)
     size_t out1_pitch;     // elements (floats)
     int W, H;
+    int y0, y1;            // centre-pixel rows [y0, y1) this launch covers (samples read the whole frame)
     int nd, ns, na;
     int hit_rule, step_mode, gi;
     // per-launch binary32 constants
@@ -508,8 +509,8 @@ __device__ __forceinline__ void gather_pixel(const GatherParams &P, int x, int y
 template <int NB, bool F16, bool INF_T, int STEP_MODE>
 __global__ void __launch_bounds__(256) gather_tile_kernel(const __grid_constant__ GatherParams P) {
     const int x = blockIdx.x * 32 + (threadIdx.x & 31);
-    const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
-    if (x >= P.W || y >= P.H) return;
+    const int y = P.y0 + blockIdx.y * 8 + (threadIdx.x >> 5);
+    if (x >= P.W || y >= P.y1) return;
     gather_pixel<NB, F16, INF_T, STEP_MODE>(P, x, y);
 }
 
@@ -521,7 +522,7 @@ template <int NB, bool F16, bool INF_T, int STEP_MODE, int MINB>
 __global__ void __launch_bounds__(128, MINB) gather_class_kernel(const __grid_constant__ GatherParams P) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int x = blockIdx.x * 128 + 4 * lane + w;
-    const int y = blockIdx.y;
+    const int y = P.y0 + blockIdx.y;
     if (x >= P.W) return;
     gather_pixel<NB, F16, INF_T, STEP_MODE>(P, x, y);
 }

@@ -15,10 +15,13 @@
 
 namespace ssilvb {
 
+// ssilvb_gather_host splits a frame into at most this many row bands (one launch each).
+constexpr int kMaxHostBands = 8;
+
 // A resolved launch choice.  Every choice gives bit-identical results.
 struct KernelChoice {
     int mapping = SSILVB_MAP_CLASS;  // single frame: SSILVB_MAP_TILE or SSILVB_MAP_CLASS
-    int minb = 9;                    // class/batch kernels: 8 or 9 blocks of 128 threads per SM
+    int minb = 8;                    // class/batch kernels: 8 (64 registers) or 9 (56) blocks of 128 threads per SM
     int rows = 1;                    // batch: rows per tile
     int ctas_per_sm = 0;             // batch: resident blocks per SM of the persistent grid (0 = occupancy)
     int graph = 1;                   // batch, persistent mode: launch through a CUDA graph
@@ -87,6 +90,15 @@ struct ssilvb_ctx {
     std::string last_error;
     void *stage = nullptr;    // staging for ssilvb_gather_host
     size_t stage_bytes = 0;
+    // ssilvb_gather_host: row bands alternate between the caller's stream and band_stream, and each
+    // band's outputs go back to the host on copy_stream while later bands still compute (created on
+    // first use)
+    cudaStream_t band_stream = nullptr;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t inputs_ready = nullptr;
+    cudaEvent_t band_done[ssilvb::kMaxHostBands] = {};
+    cudaEvent_t bands_done = nullptr;
+    cudaEvent_t copies_done = nullptr;
     ssilvb_tuning tuning = {SSILVB_MAP_AUTO, 0, 0, 0, 0, 0, {0, 0}};
     cudaStream_t cap_stream = nullptr;     // private stream the batch graphs are captured on
     std::vector<ssilvb::BatchSlot> slots;  // ring of in-flight batches

@@ -8,10 +8,10 @@ namespace ssilvb {
 template <int NB, bool F16, bool INF_T, int SM>
 cudaError_t launch_single_t(const GatherParams &P, const KernelChoice &k, cudaStream_t s) {
     if (k.mapping == SSILVB_MAP_TILE) {
-        dim3 grid((P.W + 31) / 32, (P.H + 7) / 8);
+        dim3 grid((P.W + 31) / 32, (P.y1 - P.y0 + 7) / 8);
         gather_tile_kernel<NB, F16, INF_T, SM><<<grid, 256, 0, s>>>(P);
     } else {
-        dim3 grid((P.W + 127) / 128, P.H);
+        dim3 grid((P.W + 127) / 128, P.y1 - P.y0);
         if (k.minb == 8) gather_class_kernel<NB, F16, INF_T, SM, 8><<<grid, 128, 0, s>>>(P);
         else gather_class_kernel<NB, F16, INF_T, SM, 9><<<grid, 128, 0, s>>>(P);
     }
@@ -33,12 +33,12 @@ template <int NB, bool F16, bool INF_T, int SM>
 void single_node_t(const GatherParams &P, const KernelChoice &k, const void **fn, dim3 *grid, dim3 *block) {
     if (k.mapping == SSILVB_MAP_TILE) {
         *fn = reinterpret_cast<const void *>(gather_tile_kernel<NB, F16, INF_T, SM>);
-        *grid = dim3((P.W + 31) / 32, (P.H + 7) / 8);
+        *grid = dim3((P.W + 31) / 32, (P.y1 - P.y0 + 7) / 8);
         *block = dim3(256);
     } else {
         *fn = k.minb == 8 ? reinterpret_cast<const void *>(gather_class_kernel<NB, F16, INF_T, SM, 8>)
                           : reinterpret_cast<const void *>(gather_class_kernel<NB, F16, INF_T, SM, 9>);
-        *grid = dim3((P.W + 127) / 128, P.H);
+        *grid = dim3((P.W + 127) / 128, P.y1 - P.y0);
         *block = dim3(128);
     }
 }

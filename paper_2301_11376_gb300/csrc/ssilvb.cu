@@ -4,6 +4,7 @@
 // include/ssilvb.h.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -153,6 +154,8 @@ void fill_params(ssilvb::GatherParams &P, const ssilvb_gbuffer *g, const ssilvb_
     P.out1_pitch = p->ambient_cones > 0 ? o->out1_pitch / 4 : 0;
     P.W = g->width;
     P.H = g->height;
+    P.y0 = 0;
+    P.y1 = g->height;
     P.nd = p->num_slices;
     P.ns = p->steps_per_side;
     P.na = p->ambient_cones;
@@ -316,6 +319,12 @@ ssilvb_status ssilvb_destroy(ssilvb_ctx *ctx) {
     if (ctx->stage) cudaFree(ctx->stage);
     release_batch_slots(ctx);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    for (cudaEvent_t ev : ctx->band_done)
+        if (ev) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : {ctx->inputs_ready, ctx->bands_done, ctx->copies_done})
+        if (ev) cudaEventDestroy(ev);
+    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+    if (ctx->band_stream) cudaStreamDestroy(ctx->band_stream);
     delete ctx;
     return SSILVB_OK;
 }
@@ -408,19 +417,64 @@ ssilvb_status ssilvb_gather_host(ssilvb_ctx *ctx, const ssilvb_gbuffer *gbuffer,
     ssilvb::GatherParams P;
     fill_params(P, &dg_, camera, params, &dout);
     const KernelChoice k = resolve_choice(ctx, tune_key(gbuffer, params, 0));
-    e = launch_single(P, params->sector_count, gbuffer->normal_fmt == SSILVB_FMT_F16X4, std::isinf(params->thickness),
-                      k, st);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "gather launch");
-
-    e = cudaMemcpy2DAsync(out->out0, out->out0_pitch, d_out0, W * 16, W * 16, H, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess && na > 0)
-        e = cudaMemcpy2DAsync(out->out1, out->out1_pitch, d_out1, W * 16, W * 16, H, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess && out->masks)
-        e = cudaMemcpyAsync(out->masks, d_masks, mask_bytes, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess && out->light_out)
-        e = cudaMemcpy2DAsync(out->light_out, out->light_out_pitch, d_light, W * px, W * px, H, cudaMemcpyDeviceToHost,
-                              st);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "device-to-host copy");
+    if (!ctx->copy_stream) {
+        e = cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->band_stream, cudaStreamNonBlocking);
+        for (int b = 0; e == cudaSuccess && b < kMaxHostBands; ++b)
+            e = cudaEventCreateWithFlags(&ctx->band_done[b], cudaEventDisableTiming);
+        for (cudaEvent_t *ev : {&ctx->inputs_ready, &ctx->bands_done, &ctx->copies_done})
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "copy stream set-up");
+    }
+    // Row bands of at least 256 rows, one launch each.  Every band reads the whole frame's inputs,
+    // so the inputs go first; then band b's outputs go back on the copy stream while later bands
+    // compute.  Bands alternate between two streams, so that one band's last wave overlaps the next
+    // band's first instead of draining the GPU between launches.
+    const int bands = (int)std::max<size_t>(1, std::min<size_t>(kMaxHostBands, H / 256));
+    const size_t rows = (H + bands - 1) / bands;
+    const size_t melem = params->sector_count / 8;
+    cudaStream_t cs = ctx->copy_stream;
+    e = cudaEventRecord(ctx->inputs_ready, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->band_stream, ctx->inputs_ready, 0);
+    for (int b = 0; b < bands && e == cudaSuccess; ++b) {
+        const size_t y0 = b * rows, y1 = std::min(H, y0 + rows), n = y1 - y0;
+        cudaStream_t ls = (b & 1) ? ctx->band_stream : st;
+        P.y0 = (int)y0;
+        P.y1 = (int)y1;
+        e = launch_single(P, params->sector_count, gbuffer->normal_fmt == SSILVB_FMT_F16X4,
+                          std::isinf(params->thickness), k, ls);
+        if (e != cudaSuccess) break;
+        e = cudaEventRecord(ctx->band_done[b], ls);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ctx->band_done[b], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpy2DAsync(reinterpret_cast<char *>(out->out0) + y0 * out->out0_pitch, out->out0_pitch,
+                                  reinterpret_cast<char *>(d_out0) + y0 * W * 16, W * 16, W * 16, n,
+                                  cudaMemcpyDeviceToHost, cs);
+        if (e == cudaSuccess && na > 0)
+            e = cudaMemcpy2DAsync(reinterpret_cast<char *>(out->out1) + y0 * out->out1_pitch, out->out1_pitch,
+                                  reinterpret_cast<char *>(d_out1) + y0 * W * 16, W * 16, W * 16, n,
+                                  cudaMemcpyDeviceToHost, cs);
+        for (int i = 0; e == cudaSuccess && out->masks && i < params->num_slices; ++i) {
+            const size_t o = ((size_t)i * H + y0) * W * melem;  // [N_d][H][W] words: rows y0..y1 of slice i
+            e = cudaMemcpyAsync(static_cast<char *>(out->masks) + o, static_cast<char *>(d_masks) + o, n * W * melem,
+                                cudaMemcpyDeviceToHost, cs);
+        }
+        if (e == cudaSuccess && out->light_out)
+            e = cudaMemcpy2DAsync(static_cast<char *>(out->light_out) + y0 * out->light_out_pitch,
+                                  out->light_out_pitch, static_cast<char *>(d_light) + y0 * W * px, W * px, W * px, n,
+                                  cudaMemcpyDeviceToHost, cs);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->bands_done, ctx->band_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->bands_done, 0);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->copies_done, cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->copies_done, 0);
+    if (e != cudaSuccess) {
+        // nothing enqueued so far may still write into the caller's buffers after the return
+        cudaStreamSynchronize(ctx->band_stream);
+        cudaStreamSynchronize(cs);
+        cudaStreamSynchronize(st);
+        return cuda_fail(ctx, e, "banded gather or device-to-host copy");
+    }
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "gather execution");
     return SSILVB_OK;

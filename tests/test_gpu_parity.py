@@ -155,6 +155,24 @@ def test_host_buffers_equal_device_buffers(ctx):
     del torch, ssilvb
 
 
+def test_host_buffers_in_row_bands(ctx):
+    """Host-buffer calls on frames of 256+ rows run as row-band launches whose outputs are copied
+    back while later bands compute: a ragged last band, masks of every slice and ambient output
+    must equal the single device launch bit for bit."""
+    g = scenegen.render(21, 96, 1037, 8, 3)
+    prm = Params(num_slices=3, steps_per_side=8, sector_count=64, ambient_cones=4)
+    noise, sh = scenegen.ign_table(), scenegen.sh_environment(7)
+    a = run_gpu(ctx, g, prm, noise, sh)
+    H, W = g.depth.shape
+    o0 = np.zeros((H, W, 4), np.float32)
+    o1 = np.zeros((H, W, 4), np.float32)
+    m = np.zeros((prm.num_slices, H, W), np.uint64)
+    ctx.gather_host(g.depth, g.normal, g.radiance, g.camera, prm, o0, o1, m, noise=noise, sh=sh)
+    assert np.array_equal(o0.reshape(-1, 4), a[0].astype(np.float32))
+    assert np.array_equal(o1.reshape(-1, 4), a[1].astype(np.float32))
+    assert np.array_equal(m.reshape(prm.num_slices, -1).T, a[2])
+
+
 def test_invalid_arguments_enqueue_nothing(ctx):
     import torch
 
