@@ -253,14 +253,16 @@ def hand_quad_over_sky(width: int, height: int, depth: float = 4.0, x0: int = 8,
     return GBuffer(d, n, r, cam)
 
 
-def hand_step_wall(width: int, height: int, z0: float, wall_x: float, wall_h: float) -> GBuffer:
-    """A back plane at depth z0 facing the camera, and a raised block for view-space
-    x >= wall_x whose front face is at depth z0 - wall_h (a step of height wall_h
-    toward the camera).  Pixels are classified by the exact ray hit in FP64."""
+def hand_step_wall(width: int, height: int, z0: float, wall_x: float, wall_h: float, axis: int = 0) -> GBuffer:
+    """A back plane at depth z0 facing the camera, and a raised block whose front face is at
+    depth z0 - wall_h (a step of height wall_h toward the camera): for view-space x >= wall_x
+    (axis 0), or for view-space y <= -wall_x, a ledge below the centre (axis 1).  Pixels are
+    classified by the exact ray hit in FP64."""
     fx = 0.5 * width
     cam = Camera(fx, fx, 0.5 * width, 0.5 * height)
     ys, xs = np.mgrid[0:height, 0:width]
-    a = (xs + 0.5 - cam.cx) / cam.fx
+    # view-space coordinate across the step per unit depth: x / z, or -y / z (image y points down)
+    a = (xs + 0.5 - cam.cx) / cam.fx if axis == 0 else (ys + 0.5 - cam.cy) / cam.fy
     z_top = z0 - wall_h
     x_top = a * z_top
     x_back = a * z0
@@ -269,7 +271,10 @@ def hand_step_wall(width: int, height: int, z0: float, wall_x: float, wall_h: fl
     n = np.zeros((height, width, 4), dtype=np.float32)
     n[..., 2] = 1.0
     side = (x_top < wall_x) & (x_back >= wall_x)
-    n[side, 0] = -1.0
+    if axis == 0:
+        n[side, 0] = -1.0  # the side face looks back toward -x
+    else:
+        n[side, 1] = 1.0   # the ledge's side face looks up, toward +y
     n[side, 2] = 0.0
     r = np.zeros((height, width, 4), dtype=np.float32)
     r[..., :3] = 0.25

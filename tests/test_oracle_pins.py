@@ -166,24 +166,37 @@ def test_infinite_thickness_equals_quantised_horizon(nb):
 
 # --- single infinite wall: closed-form occluded fraction (Section 3.1) ------------------------
 
+@pytest.mark.parametrize("axis", [0, 1])
 @pytest.mark.parametrize("thickness", [INF, 2.0])
-def test_step_wall_closed_form(thickness):
+def test_step_wall_closed_form(thickness, axis):
     """Centre pixel on the back plane at the principal point (gamma = 0).  A wall face at
-    x = X_w rises H_w toward the camera; on slice phi the top edge is at in-plane distance
-    X_w/|cos phi|, so the occluded sectors on the wall side are N_b (pi/2 - h*)/pi with
-    h* = atan2(X_w/|cos phi|, H_w).  Holds for t = inf and any t >= H_w."""
+    x = X_w (axis 0), or a ledge edge at y = -X_w below the centre (axis 1), rises H_w toward
+    the camera.  Slice phi steps along (cos phi, sin phi) in pixels with image y down, i.e.
+    along view (cos phi, -sin phi); with c the component of that direction toward the step,
+    its top edge is at in-plane distance X_w/|c|, and the occluded sectors are the
+    N_b (pi/2 - h*)/pi nearest the hemisphere edge of the side facing it (sectors N_b-1 down
+    for side +omega, 0 up for side -omega), h* = atan2(X_w/|c|, H_w).  Holds for t = inf and
+    any t >= H_w."""
     W = H = 255
     z0, xw, hw, nb = 4.0, 0.6, 1.5, 32
-    g = scenegen.hand_step_wall(W, H, z0, xw, hw)
+    g = scenegen.hand_step_wall(W, H, z0, xw, hw, axis=axis)
     prm = Params(num_slices=4, steps_per_side=48, radius=3.0, thickness=thickness, sector_count=nb)
     c = (W - 1) // 2
     _, _, masks, _ = oracle.fp64(oracle.Problem(g, prm, None), pixels=[(c, c)])
+    half = (1 << (nb // 2)) - 1
     for i in range(4):
         phi = i * math.pi / 4
-        cphi = abs(math.cos(phi))
-        expect = 0.0 if cphi < 1e-9 else nb * (math.pi / 2 - math.atan2(xw / cphi, hw)) / math.pi
-        got = bin(int(masks[0, i])).count("1")
-        assert abs(got - expect) <= 1.0, (i, got, expect)
+        toward = math.cos(phi) if axis == 0 else math.sin(phi)  # +x, or -y in view space
+        m = int(masks[0, i])
+        if abs(toward) < 1e-9:
+            assert m == 0, (i, hex(m))
+            continue
+        expect = nb * (math.pi / 2 - math.atan2(xw / abs(toward), hw)) / math.pi
+        assert abs(bin(m).count("1") - expect) <= 1.0, (i, bin(m).count("1"), expect)
+        if toward > 0:   # side +omega faces the step: a run ending at sector N_b - 1
+            assert m & half == 0 and m >> (nb - 1) == 1, (i, hex(m))
+        else:            # side -omega faces it: a run starting at sector 0
+            assert m >> (nb // 2) == 0 and m & 1 == 1, (i, hex(m))
 
 
 # --- single sample: closed-form indirect light (Algorithm 1 GI line, Section 3.3) -------------
@@ -238,6 +251,67 @@ def test_single_sample_gi_closed_form():
     r0, _, rmask = oracle.fp32(oracle.Problem(g, prm, None), pixels=[(c, c)])
     assert int(rmask[0, 0]) == m
     np.testing.assert_allclose(r0[0, :3], gi, atol=2e-6)
+
+
+def test_two_overlapping_samples_credit_the_nearer_first():
+    """Section 3.3: samples are taken near to far and a sector's indirect light comes from the
+    first sample that occludes it.  Two samples on the +omega side of slice 0 (steps 0 and 1)
+    whose sector runs overlap in part: the far sample contributes only its sectors the near
+    one left free.  Crediting the last sample, or both, gives a different GI."""
+    W = H = 41
+    fx = 20.5
+    cam = scenegen.Camera(fx, fx, 20.5, 20.5)
+    c = 20
+    radius, ns, nb, t = 2.0, 4, 32, 0.5
+    z = 3.0
+    offs = G.sample_offsets(radius, fx, z, ns)
+    dq = [int(np.rint(offs[0])), int(np.rint(offs[1]))]
+    zq = [float(np.float32(2.6)), float(np.float32(2.2))]  # the values the depth plane holds
+    nq = [np.array([-0.9, 0.0, 0.436], dtype=np.float32), np.array([-0.95, 0.0, 0.312], dtype=np.float32)]
+    cq = [np.array([0.9, 0.1, 0.1], dtype=np.float32), np.array([0.1, 0.8, 0.3], dtype=np.float32)]
+    depth = np.full((H, W), np.inf, dtype=np.float32)
+    nrm = np.zeros((H, W, 4), dtype=np.float32)
+    rad = np.zeros((H, W, 4), dtype=np.float32)
+    depth[c, c] = z
+    nrm[c, c, :3] = (0.0, 0.0, 1.0)
+    for k in range(2):
+        depth[c, c + dq[k]] = zq[k]
+        nrm[c, c + dq[k], :3] = nq[k]
+        rad[c, c + dq[k], :3] = cq[k]
+    g = scenegen.GBuffer(depth, nrm, rad, cam)
+    prm = Params(num_slices=1, steps_per_side=ns, radius=radius, thickness=t, sector_count=nb)
+
+    n_p = np.array([0.0, 0.0, 1.0])
+    p, v, s, gamma = G.frame(cam, c, c, z, n_p, np.float32(1.0), np.float32(0.0))
+    masks, weights = [], []
+    for k in range(2):
+        sf = G.unproject(cam, c + dq[k] + 0.5, c + 0.5, zq[k])
+        l = sf - p
+        sb = sf + t * p / np.linalg.norm(p)
+        hf = math.acos(np.dot(l, v) / np.linalg.norm(l))
+        hb = math.acos(np.dot(sb - p, v) / np.linalg.norm(sb - p))
+        A, B = sorted([G.sector_coord(hf, gamma, nb), G.sector_coord(hb, gamma, nb)])
+        masks.append(G.half_covered_mask(A, B, nb))
+        lh = l / np.linalg.norm(l)
+        weights.append(max(0.0, float(np.dot(n_p, lh))) * max(0.0, -float(np.dot(nq[k].astype(np.float64), lh))))
+    m0, m1 = masks
+    pop = lambda m: bin(m).count("1")
+    # the scene does what the test needs: partial overlap, both samples lit
+    assert pop(m0 & m1) >= 2 and pop(m1 & ~m0) >= 2 and pop(m0 & ~m1) >= 2
+    assert min(weights) > 0.1
+    c64 = [x.astype(np.float64) for x in cq]
+    first = (pop(m0) * weights[0] * c64[0] + pop(m1 & ~m0) * weights[1] * c64[1]) / nb
+    last = (pop(m0 & ~m1) * weights[0] * c64[0] + pop(m1) * weights[1] * c64[1]) / nb
+    both = (pop(m0) * weights[0] * c64[0] + pop(m1) * weights[1] * c64[1]) / nb
+    assert np.abs(first - last).max() > 1e-2 and np.abs(first - both).max() > 1e-2
+
+    o0, _, m, _ = oracle.fp64(oracle.Problem(g, prm, None), pixels=[(c, c)])
+    assert int(m[0, 0]) == m0 | m1
+    np.testing.assert_allclose(o0[0, :3], first, rtol=1e-12, atol=1e-15)
+    assert abs(o0[0, 3] - (1.0 - pop(m0 | m1) / nb)) < 1e-15
+    r0, _, rm = oracle.fp32(oracle.Problem(g, prm, None), pixels=[(c, c)])
+    assert int(rm[0, 0]) == m0 | m1
+    np.testing.assert_allclose(r0[0, :3], first, atol=2e-6)
 
 
 # --- monotonicity (Section 3.1: samples only add occlusion; thicker slabs cover more) ---------
