@@ -7,7 +7,8 @@ boundary; (G2) AO, GI and ambient within 1e-4 of the FP64 oracle on every pixel 
 whose hit-rule decisions lies within 1e-4 sector units of a boundary.  On the remaining pixels the two
 precisions may credit a sector to different samples (GI credits each sector to the first
 sample that covers it) or flip it: there the difference is bounded by a few sectors' share,
-and such pixels must stay rare."""
+and such pixels must stay rare.  (G4) The mean absolute error against FP64 over every
+compared pixel is at most 1e-4."""
 import numpy as np
 
 import oracle
@@ -103,11 +104,17 @@ def check_parity(g, prm, noise, sh, gpu, pixels=None, min_agree=0.98):
     assert np.abs(g0[near] - e0[near]).max(initial=0.0) <= few
     if prm.ambient_cones > 0:
         assert np.abs(g1[near] - e1[near]).max(initial=0.0) <= 2.0 * few
+    # G4: the mean error over every compared pixel, near-boundary ones included
+    mean0 = float(np.abs(g0 - e0).mean())
+    assert mean0 <= TOL, mean0
+    if prm.ambient_cones > 0:
+        assert float(np.abs(g1 - e1).mean()) <= TOL
     # GPU vs replica: the same binary32 sequence, so only accumulation-order effects remain
     assert np.abs(g0 - r0).max(initial=0.0) <= 1e-6
     if prm.ambient_cones > 0:
         assert np.abs(g1 - r1).max(initial=0.0) <= 1e-6
-    return {"agree": float(agree.mean()), "clear": float(clear.mean()), "err_fp64": float(err0), "n": len(xy)}
+    return {"agree": float(agree.mean()), "clear": float(clear.mean()), "err_fp64": float(err0), "mean_err_fp64": mean0,
+            "n": len(xy)}
 
 
 def sample_pixels(H, W, n, seed=0):
