@@ -311,6 +311,27 @@ ssilvb_status ssilvb_create(ssilvb_ctx **out_ctx, int cuda_device) {
     return SSILVB_OK;
 }
 
+// The streams and events of the banded host-buffer path, all or none (a partial set is released).
+static void release_host_streams(ssilvb_ctx *ctx) {
+    for (cudaEvent_t &ev : ctx->band_done)
+        if (ev) cudaEventDestroy(ev), ev = nullptr;
+    for (cudaEvent_t *ev : {&ctx->inputs_ready, &ctx->bands_done, &ctx->copies_done})
+        if (*ev) cudaEventDestroy(*ev), *ev = nullptr;
+    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream), ctx->copy_stream = nullptr;
+    if (ctx->band_stream) cudaStreamDestroy(ctx->band_stream), ctx->band_stream = nullptr;
+}
+
+static cudaError_t create_host_streams(ssilvb_ctx *ctx) {
+    cudaError_t e = cudaStreamCreateWithFlags(&ctx->band_stream, cudaStreamNonBlocking);
+    for (int b = 0; e == cudaSuccess && b < kMaxHostBands; ++b)
+        e = cudaEventCreateWithFlags(&ctx->band_done[b], cudaEventDisableTiming);
+    for (cudaEvent_t *ev : {&ctx->inputs_ready, &ctx->bands_done, &ctx->copies_done})
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) release_host_streams(ctx);  // copy_stream doubles as the "created" flag
+    return e;
+}
+
 ssilvb_status ssilvb_destroy(ssilvb_ctx *ctx) {
     if (!ctx) return SSILVB_OK;
     DeviceGuard dg(ctx->device);
@@ -319,12 +340,7 @@ ssilvb_status ssilvb_destroy(ssilvb_ctx *ctx) {
     if (ctx->stage) cudaFree(ctx->stage);
     release_batch_slots(ctx);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
-    for (cudaEvent_t ev : ctx->band_done)
-        if (ev) cudaEventDestroy(ev);
-    for (cudaEvent_t ev : {ctx->inputs_ready, ctx->bands_done, ctx->copies_done})
-        if (ev) cudaEventDestroy(ev);
-    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
-    if (ctx->band_stream) cudaStreamDestroy(ctx->band_stream);
+    release_host_streams(ctx);
     delete ctx;
     return SSILVB_OK;
 }
@@ -418,12 +434,7 @@ ssilvb_status ssilvb_gather_host(ssilvb_ctx *ctx, const ssilvb_gbuffer *gbuffer,
     fill_params(P, &dg_, camera, params, &dout);
     const KernelChoice k = resolve_choice(ctx, tune_key(gbuffer, params, 0));
     if (!ctx->copy_stream) {
-        e = cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->band_stream, cudaStreamNonBlocking);
-        for (int b = 0; e == cudaSuccess && b < kMaxHostBands; ++b)
-            e = cudaEventCreateWithFlags(&ctx->band_done[b], cudaEventDisableTiming);
-        for (cudaEvent_t *ev : {&ctx->inputs_ready, &ctx->bands_done, &ctx->copies_done})
-            if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+        e = create_host_streams(ctx);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "copy stream set-up");
     }
     // Row bands of at least 256 rows, one launch each.  Every band reads the whole frame's inputs,
