@@ -56,12 +56,18 @@ def make_workload(name, nb):
     return scenegen.workload_256()
 
 
+KERNEL_SOURCES = ["gather_kernel.cuh", "launch_impl.cuh", "launch_nb32.cu", "launch_nb64.cu", "launch_nb128.cu"]
+
+
 def kernel_sources_sha256():
-    """Hash of the CUDA sources and the ABI header: measured counters apply only to this code."""
+    """Hash of the device code (the kernel and its instantiating units) and the nvcc flags:
+    measured DRAM counters apply only to this code; host-side changes leave them valid."""
     import hashlib
-    h = hashlib.sha256()
+
+    import paper_2301_11376_gb300 as ssilvb
+    h = hashlib.sha256(" ".join(ssilvb.NVCC_FLAGS).encode())
     csrc = os.path.join(ROOT, "paper_2301_11376_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)) + ["../../include/ssilvb.h"]:
+    for f in KERNEL_SOURCES:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(f.encode() + b"\0" + fh.read())
     return h.hexdigest()
