@@ -437,18 +437,27 @@ ssilvb_status ssilvb_gather_host(ssilvb_ctx *ctx, const ssilvb_gbuffer *gbuffer,
         e = create_host_streams(ctx);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "copy stream set-up");
     }
-    // Row bands of at least 256 rows, one launch each.  Every band reads the whole frame's inputs,
-    // so the inputs go first; then band b's outputs go back on the copy stream while later bands
-    // compute.  Bands alternate between two streams, so that one band's last wave overlaps the next
-    // band's first instead of draining the GPU between launches.
+    // Row bands, one launch each, for frames of 512+ rows.  Every band reads the whole frame's
+    // inputs, so the inputs go first; then band b's outputs go back on the copy stream while later
+    // bands compute.  Bands alternate between two streams, so that one band's last wave overlaps
+    // the next band's first instead of draining the GPU between launches.  Band b gets a share of
+    // the rows proportional to 10 - b: the last band, whose copy nothing hides, is the smallest.
     const int bands = (int)std::max<size_t>(1, std::min<size_t>(kMaxHostBands, H / 256));
-    const size_t rows = (H + bands - 1) / bands;
+    size_t cut[kMaxHostBands + 1] = {0};
+    {
+        size_t wsum = 0, w = 0;
+        for (int b = 0; b < bands; ++b) wsum += 10 - b;
+        for (int b = 0; b < bands; ++b) {
+            w += 10 - b;
+            cut[b + 1] = H * w / wsum;
+        }
+    }
     const size_t melem = params->sector_count / 8;
     cudaStream_t cs = ctx->copy_stream;
     e = cudaEventRecord(ctx->inputs_ready, st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->band_stream, ctx->inputs_ready, 0);
     for (int b = 0; b < bands && e == cudaSuccess; ++b) {
-        const size_t y0 = b * rows, y1 = std::min(H, y0 + rows), n = y1 - y0;
+        const size_t y0 = cut[b], y1 = cut[b + 1], n = y1 - y0;
         cudaStream_t ls = (b & 1) ? ctx->band_stream : st;
         P.y0 = (int)y0;
         P.y1 = (int)y1;
