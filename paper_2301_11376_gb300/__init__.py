@@ -274,8 +274,10 @@ class Context:
                                            ctypes.byref(pc), ctypes.byref(o), ctypes.c_void_p(s.cuda_stream)))
 
     def gather_host(self, depth, normal, radiance, camera, params, out0, out1=None, masks=None, noise=None, sh=None,
-                    stream=None):
-        """ssilvb_gather_host on host arrays (numpy or CPU tensors, ideally pinned); synchronous."""
+                    stream=None, light_out=None, direct=None):
+        """ssilvb_gather_host on host arrays (numpy or CPU tensors, ideally pinned); synchronous.
+        light_out / direct: the multi-bounce light buffer and this frame's direct light, in the
+        radiance format."""
         def ptr(a):
             return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
 
@@ -287,11 +289,13 @@ class Context:
         rfmt = FMT_F16X4 if (str(radiance.dtype).endswith("float16")) else FMT_F32X4
         H, W = depth.shape[:2]
         g = Gbuffer(W, H, ptr(depth), pitch(depth), ptr(normal), pitch(normal), nfmt, ptr(radiance), pitch(radiance),
-                    rfmt)
+                    rfmt, ptr(direct) if direct is not None else None, pitch(direct) if direct is not None else 0)
         keep = _HostArrays()
         pc = _params_c(params, keep, noise, sh)
         o = Output(ptr(out0), pitch(out0), ptr(out1) if out1 is not None else None,
-                   pitch(out1) if out1 is not None else 0, ptr(masks) if masks is not None else None)
+                   pitch(out1) if out1 is not None else 0, ptr(masks) if masks is not None else None,
+                   ptr(light_out) if light_out is not None else None,
+                   pitch(light_out) if light_out is not None else 0)
         sh_ = stream.cuda_stream if stream is not None else None
         self._check(self.lib.ssilvb_gather_host(self.handle, ctypes.byref(g), ctypes.byref(_camera_c(camera)),
                                                 ctypes.byref(pc), ctypes.byref(o), ctypes.c_void_p(sh_)))

@@ -155,22 +155,39 @@ def test_host_buffers_equal_device_buffers(ctx):
     del torch, ssilvb
 
 
-def test_host_buffers_in_row_bands(ctx):
-    """Host-buffer calls on frames of 256+ rows run as row-band launches whose outputs are copied
-    back while later bands compute: a ragged last band, masks of every slice and ambient output
-    must equal the single device launch bit for bit."""
+@pytest.mark.parametrize("f16", [False, True])
+def test_host_buffers_in_row_bands(ctx, f16):
+    """Host-buffer calls on frames of 512+ rows run as row-band launches whose outputs are copied
+    back while later bands compute: uneven bands, masks of every slice, ambient output and the
+    multi-bounce light buffer must equal the single device launch bit for bit."""
+    import torch
     g = scenegen.render(21, 96, 1037, 8, 3)
-    prm = Params(num_slices=3, steps_per_side=8, sector_count=64, ambient_cones=4)
+    if f16:
+        g = g.as_f16()
+    prm = Params(num_slices=3, steps_per_side=8, sector_count=64, ambient_cones=4, bounce_gain=0.7)
     noise, sh = scenegen.ign_table(), scenegen.sh_environment(7)
-    a = run_gpu(ctx, g, prm, noise, sh)
     H, W = g.depth.shape
+    direct = np.ascontiguousarray((g.radiance * 0.5).astype(g.radiance.dtype))
+    # the device launch
+    d, n, r = (torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (g.depth, g.normal, g.radiance))
+    dd = torch.from_numpy(direct).cuda()
+    import paper_2301_11376_gb300 as ssilvb
+    do0, do1, dm = ssilvb.alloc_outputs(H, W, prm, "cuda", masks=True)
+    dlo = torch.zeros_like(r)
+    ctx.gather(d, n, r, g.camera, prm, do0, do1, dm, noise=noise, sh=sh, light_out=dlo, direct=dd)
+    torch.cuda.synchronize()
+    # the same frame through host buffers
     o0 = np.zeros((H, W, 4), np.float32)
     o1 = np.zeros((H, W, 4), np.float32)
     m = np.zeros((prm.num_slices, H, W), np.uint64)
-    ctx.gather_host(g.depth, g.normal, g.radiance, g.camera, prm, o0, o1, m, noise=noise, sh=sh)
-    assert np.array_equal(o0.reshape(-1, 4), a[0].astype(np.float32))
-    assert np.array_equal(o1.reshape(-1, 4), a[1].astype(np.float32))
-    assert np.array_equal(m.reshape(prm.num_slices, -1).T, a[2])
+    lo = np.zeros_like(g.radiance)
+    ctx.gather_host(g.depth, g.normal, g.radiance, g.camera, prm, o0, o1, m, noise=noise, sh=sh,
+                    light_out=lo, direct=direct)
+    assert np.array_equal(o0, do0.cpu().numpy())
+    assert np.array_equal(o1, do1.cpu().numpy())
+    assert np.array_equal(m.view(np.int32).reshape(-1), dm.cpu().numpy().reshape(-1))  # [N_d][H][W] u64 words
+    assert np.array_equal(lo, dlo.cpu().numpy())
+    assert np.abs(lo[..., :3].astype(np.float64)).max() > 0
 
 
 def test_invalid_arguments_enqueue_nothing(ctx):
