@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ssilvb", choices=["ssilvb", "reference"])
     ap.add_argument("--workload", default="4k",
-                    choices=["4k", "1080p", "256", "batch", "serve", "trends", "precision"])
+                    choices=["4k", "1080p", "256", "batch", "serve", "trends", "precision", "issue_peak"])
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--nb", type=int, default=32)
     ap.add_argument("--no-e2e", action="store_true")
@@ -497,6 +497,94 @@ def run_serve_bench(args, world, rank, local):
            "clocks": clk, "gpu_launches": a["batches"]}
     print(json.dumps(out))
 
+# Issue-rate probe: the denominators of the ALU roofline measured on this GPU (scalar FP32 FMA,
+# packed f32x2 FMA, integer ops), each from 8 independent chains per thread on 8 blocks of 256
+# threads per SM.  Nothing here touches the gather.
+ISSUE_PROBE_CU = r"""
+#include <cstdio>
+#include <cuda_runtime.h>
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm volatile("{.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+                 "mov.b64 rc, {%6, %7};\n\tfma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;}"
+                 : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+__global__ void k_ffma(float *out, int n, float m) {
+    float a[8];
+    for (int i = 0; i < 8; ++i) a[i] = threadIdx.x * 1e-3f + i;
+    for (int it = 0; it < n; ++it)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) a[i] = fmaf(a[i], m, 0.5f);
+    float s = 0; for (int i = 0; i < 8; ++i) s += a[i];
+    if (s == 12345.0f) out[0] = s;
+}
+__global__ void k_ffma2(float *out, int n, float m) {
+    float2 a[8];
+    for (int i = 0; i < 8; ++i) a[i] = make_float2(threadIdx.x * 1e-3f + i, i * 0.5f);
+    const float2 mm = make_float2(m, m), h = make_float2(0.5f, 0.25f);
+    for (int it = 0; it < n; ++it)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) a[i] = pfma(a[i], mm, h);
+    float s = 0; for (int i = 0; i < 8; ++i) s += a[i].x + a[i].y;
+    if (s == 12345.0f) out[0] = s;
+}
+__global__ void k_int(int *out, int n, int m) {
+    int a[8];
+    for (int i = 0; i < 8; ++i) a[i] = threadIdx.x + i;
+    for (int it = 0; it < n; ++it)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) a[i] = (a[i] ^ m) + i;
+    int s = 0; for (int i = 0; i < 8; ++i) s += a[i];
+    if (s == 12345) out[0] = s;
+}
+int main() {
+    int sms; cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+    float *out; if (cudaMalloc(&out, 16) != cudaSuccess) return 1;
+    const int n = 1 << 14, blocks = sms * 8, threads = 256;
+    const double elems = (double)blocks * threads * n * 8;
+    cudaEvent_t e0, e1; cudaEventCreate(&e0); cudaEventCreate(&e1);
+    float t[3] = {0, 0, 0};
+    for (int rep = 0; rep < 2; ++rep) {  // the first pass warms the clocks up
+        cudaEventRecord(e0); k_ffma<<<blocks, threads>>>(out, n, 0.999f); cudaEventRecord(e1); cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&t[0], e0, e1);
+        cudaEventRecord(e0); k_ffma2<<<blocks, threads>>>(out, n, 0.999f); cudaEventRecord(e1); cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&t[1], e0, e1);
+        cudaEventRecord(e0); k_int<<<blocks, threads>>>((int *)out, n, 7); cudaEventRecord(e1); cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&t[2], e0, e1);
+    }
+    printf("%d %.6f %.6f %.6f %.1f\n", sms, t[0], t[1], t[2], elems);
+    return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+"""
+
+
+def run_issue_peak(args, world, rank, local):
+    """ALU roofline denominators measured here, beside the derived peak the roofline uses."""
+    if rank != 0:
+        return
+    import subprocess
+    import tempfile
+    with tempfile.TemporaryDirectory() as d:
+        src, exe = os.path.join(d, "issue_probe.cu"), os.path.join(d, "issue_probe")
+        with open(src, "w") as f:
+            f.write(ISSUE_PROBE_CU)
+        subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", exe, src], check=True)
+        clocks = Clocks(local)
+        clocks.start()
+        r = subprocess.run([exe], check=True, capture_output=True, text=True)
+        clk = clocks.stop()
+    sms, t_ffma, t_ffma2, t_int, elems = r.stdout.split()
+    sms, elems = int(sms), float(elems)
+    derived = sms * FP32_LANES_PER_SM * 2.070e9 / 1e12
+    out = {"metric": "ALU issue-rate probe (roofline denominators)", "unit": "T lane-ops/s", "n_gpus": 1,
+           "derived_peak": derived, "derived_note": f"{sms} SMs x 128 lanes x 2.070 GHz",
+           "ffma_fp32_ops": elems / float(t_ffma) / 1e9,
+           "ffma2_instructions": elems / float(t_ffma2) / 1e9, "ffma2_fp32_ops": 2 * elems / float(t_ffma2) / 1e9,
+           "int_xor_add_ops": 2 * elems / float(t_int) / 1e9, "clocks": clk}
+    out["value"] = out["ffma_fp32_ops"]
+    print(json.dumps(out))
+
 
 def main():
     args = parse()
@@ -512,6 +600,9 @@ def main():
         return
     if args.workload == "trends":
         run_trend_sweep(args, world, rank, local)
+        return
+    if args.workload == "issue_peak":
+        run_issue_peak(args, world, rank, local)
         return
     if args.workload == "precision":
         run_precision_study(args, world, rank, local)
