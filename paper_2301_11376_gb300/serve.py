@@ -5,8 +5,9 @@ Requests name a G-buffer that stays resident on the device and carry their own p
 soon as an in-flight slot and output memory are free, launches each batch with
 ``ssilvb_gather_batch`` on one of several streams (so batches overlap on the GPU), and
 records each request's completion on the device clock.  Output memory comes from one
-device arena with a first-fit free list; a request waits while its outputs do not fit, and
-arrivals beyond a bounded queue are shed and counted.
+device arena with a first-fit free list; a request waits while its outputs do not fit.  The
+bound on the system counts every admitted request not yet complete, queued or on the GPU;
+arrivals beyond it are shed and counted.
 
 ``PlainServer`` is the naive baseline: one request at a time, one ``ssilvb_gather`` launch
 and one host synchronisation per request, same queue bound.
@@ -133,13 +134,14 @@ class Server:
         base.synchronize()
         t0 = time.perf_counter()
         i, si = 0, 0
+        n_inflight = 0  # requests in the batches on the GPU
         last_done = 0.0
         while i < len(reqs) or pending or inflight:
             now = time.perf_counter() - t0
             if now > timeout_s:
                 raise RuntimeError("serving run exceeded its time limit")
             while i < len(reqs) and reqs[i].arrival <= now:
-                if len(pending) < self.max_queue:
+                if len(pending) + n_inflight < self.max_queue:
                     pending.append(reqs[i])
                 else:
                     st.dropped += 1
@@ -147,6 +149,7 @@ class Server:
             # completions, in launch order
             while inflight and inflight[0][0].query():
                 ev, items = inflight.popleft()
+                n_inflight -= len(items)
                 t_done = base.elapsed_time(ev) / 1e3
                 last_done = max(last_done, t_done)
                 for req, off, nb_, o0, o1 in items:
@@ -189,6 +192,7 @@ class Server:
                     ev = torch.cuda.Event(enable_timing=True)
                     ev.record(s)
                     inflight.append((ev, batch))
+                    n_inflight += len(batch)
                     st.batches += 1
                     st.max_inflight_seen = max(st.max_inflight_seen, len(inflight))
                     continue
