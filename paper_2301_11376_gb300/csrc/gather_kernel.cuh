@@ -157,7 +157,7 @@ __device__ __forceinline__ float2 own_acos_pair(float2 c) {
 constexpr float kMagic = 12582912.0f;
 constexpr int kMagicBits = 0x4B400000;
 
-// Bits [lo, lo + cnt) of a 32-bit word (0 when lo >= 32 or cnt == 0).
+// Bits [lo, min(lo + cnt, 32)) of a 32-bit word, lo, cnt >= 0 (0 when lo >= 32 or cnt == 0).
 __device__ __forceinline__ uint32_t run32(int lo, int cnt) {
     uint32_t r;
     asm("bmsk.clamp.b32 %0, %1, %2;" : "=r"(r) : "r"(lo), "r"(cnt));
@@ -192,20 +192,24 @@ template <> struct MaskT<128> { using T = Mask128; };
 
 template <int NB> __device__ __forceinline__ typename MaskT<NB>::T run_mask(int lo, int hi);
 template <> __device__ __forceinline__ uint32_t run_mask<32>(int lo, int hi) { return run32(lo, hi - lo); }
+// Runs for 64 and 128 sectors (0 <= lo <= hi): word i holds sectors [32 i, 32 i + 32); bmsk.clamp
+// clips a run at the top of its word by itself, so only the start needs moving into the word.
 template <> __device__ __forceinline__ unsigned long long run_mask<64>(int lo, int hi) {
-    const int a0 = min(lo, 32), e0 = min(hi, 32);
-    const int a1 = max(lo - 32, 0), e1 = max(hi - 32, 0);
-    const uint32_t w0 = run32(a0, max(e0 - a0, 0));
-    const uint32_t w1 = run32(a1, max(e1 - a1, 0));
-    return ((unsigned long long)w1 << 32) | w0;
+    const uint32_t w0 = run32(lo, hi - lo);
+    const int a1 = max(lo - 32, 0);
+    const uint32_t w1 = run32(a1, max(hi - 32 - a1, 0));
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "r"(w0), "r"(w1));
+    return r;
 }
 
 template <> __device__ __forceinline__ Mask128 run_mask<128>(int lo, int hi) {
     Mask128 r;
+    r.w[0] = run32(lo, hi - lo);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int a = min(max(lo - 32 * i, 0), 32), e = min(max(hi - 32 * i, 0), 32);
-        r.w[i] = run32(a, max(e - a, 0));
+    for (int i = 1; i < 4; ++i) {
+        const int a = max(lo - 32 * i, 0);
+        r.w[i] = run32(a, max(hi - 32 * i - a, 0));
     }
     return r;
 }
