@@ -6,7 +6,8 @@
 //
 // The binary32 operation sequence on the bitmask path is fixed: round to
 // nearest even, fused multiply-adds only where fmaf() is written (the file is
-// built with -fmad=false), IEEE sqrt, no flush to zero.  Integer decisions
+// built with -fmad=false; pfma/pmul/psub do two of the listed operations at
+// once, each half exactly the scalar one), IEEE sqrt, no flush to zero.  Integer decisions
 // taken from floating point (which pixel a step reads, which sectors a sample
 // covers) are therefore reproducible bit for bit on any IEEE machine.
 //
