@@ -53,6 +53,9 @@ SMALL = [
     (64, 48, 15, dict(num_slices=3, steps_per_side=12, sector_count=128, ambient_cones=8), True),
     (45, 37, 16, dict(num_slices=2, steps_per_side=9, sector_count=128, thickness=math.inf, hit_rule=1), True),
     (50, 41, 17, dict(num_slices=5, steps_per_side=7, sector_count=128, step_mode=1, thickness_slope=0.03), True),
+    (40, 30, 18, dict(num_slices=2, steps_per_side=1), True),                  # one step: a pair's second half idle
+    (40, 30, 19, dict(num_slices=2, steps_per_side=6, radius=1e6), True),      # projected radius at its 2^20 cap
+    (40, 30, 20, dict(num_slices=2, steps_per_side=6, radius=1e-4), True),     # every step on the centre pixel
 ]
 
 
@@ -75,6 +78,28 @@ def test_fp16_storage(ctx, f16):
     noise, sh = scenegen.ign_table(), scenegen.sh_environment(7)
     res = run_gpu(ctx, g, prm, noise, sh)
     check_parity(g, prm, noise, sh, res)
+
+
+@pytest.mark.parametrize("nb,step_mode,f16", [(32, 0, True), (64, 1, False), (128, 0, False)])
+def test_launch_choices_bit_identical(ctx, nb, step_mode, f16):
+    """Every single-frame launch choice (class-strided warps with the 8- or 9-block register
+    budget, natural 32x8 tiles) computes the same binary32 sequence: identical bits."""
+    g = scenegen.render(22, 150, 77, 8, 3)
+    if f16:
+        g = g.as_f16()
+    prm = Params(num_slices=3, steps_per_side=9, sector_count=nb, step_mode=step_mode, ambient_cones=4)
+    noise, sh = scenegen.ign_table(), scenegen.sh_environment(7)
+    results = []
+    try:
+        for mapping, occupancy in ((2, 8), (2, 9), (1, 0)):
+            ctx.set_tuning(mapping=mapping, occupancy=occupancy)
+            results.append(run_gpu(ctx, g, prm, noise, sh))
+    finally:
+        ctx.set_tuning()
+    for r in results[1:]:
+        for a, b in zip(results[0], r):
+            assert np.array_equal(a, b)
+    check_parity(g, prm, noise, sh, results[0])
 
 
 def test_pitched_inputs(ctx):
