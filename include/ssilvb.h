@@ -245,7 +245,9 @@ ssilvb_status ssilvb_set_tuning(ssilvb_ctx *ctx, const ssilvb_tuning *tuning);
 
 /* Wait for the work enqueued on stream and report a failure of it: CUDA
  * (asynchronous launch or execution error) or DEVICE_CHECK / TIMEOUT from the
- * context's device status word, which the call then clears. */
+ * context's device status word, which the call then clears.  The current kernels
+ * neither wait on the device nor check anything there (every argument is checked on
+ * the host before a launch), so those two codes are reserved and never returned. */
 ssilvb_status ssilvb_synchronize(ssilvb_ctx *ctx, struct CUstream_st *stream);
 
 #ifdef __cplusplus
