@@ -181,7 +181,8 @@ ssilvb_status run_batch(ssilvb_ctx *ctx, const ssilvb_frame *frames, int n, cuda
         return SSILVB_OK;
     }
 
-    // Work list: every frame's bands of k.rows rows x 128 pixels, concatenated in frame order.
+    // Work list: every frame's tiles (k.rows patch rows of one patch column and row class; see
+    // gather_batch_kernel), concatenated in frame order.
     BatchHeader *hdr = reinterpret_cast<BatchHeader *>(s.h_table);
     FrameDesc *fd = reinterpret_cast<FrameDesc *>(s.h_table + sizeof(BatchHeader));
     long long tiles = 0;
@@ -189,10 +190,10 @@ ssilvb_status run_batch(ssilvb_ctx *ctx, const ssilvb_frame *frames, int n, cuda
         const ssilvb_frame &f = frames[i];
         std::memset(&fd[i], 0, sizeof(FrameDesc));
         fill_params(fd[i].P, &f.gbuffer, &f.camera, &f.params, &f.out);
-        fd[i].tiles_x = (f.gbuffer.width + 127) / 128;
+        fd[i].tiles_x = 4 * ((f.gbuffer.width + 31) / 32);
         fd[i].rows = k.rows;
         fd[i].tile_begin = (int)tiles;
-        tiles += (long long)fd[i].tiles_x * ((f.gbuffer.height + k.rows - 1) / k.rows);
+        tiles += (long long)fd[i].tiles_x * ((f.gbuffer.height + 16 * k.rows - 1) / (16 * k.rows));
     }
     if (tiles >= (1LL << 31) - (1LL << 24)) return fail(ctx, SSILVB_ERR_INVALID_ARG, "batch has too many work items");
     std::memset(hdr, 0, sizeof(BatchHeader));

@@ -519,30 +519,40 @@ __global__ void __launch_bounds__(256) gather_tile_kernel(const __grid_constant_
     gather_pixel<NB, F16, INF_T, STEP_MODE>(P, x, y);
 }
 
-// Class-strided mapping: a block covers 128 consecutive pixels of one row; warp w takes the
-// pixels with x = 4 * lane + w, so all 32 lanes share a 4x4 noise class and therefore the
-// slice directions and step offsets: their samples land on neighbouring pixels and their
-// skip decisions agree.  MINB: blocks of 128 threads per SM the register budget is sized for.
+// Class-strided mapping.  A warp takes 8 x 4 pixels at stride 4 of a 32 x 16 pixel patch, all of
+// one 4x4 noise class, so its 32 lanes share the slice directions and step offsets: their samples
+// land on neighbouring pixels and their skip decisions mostly agree (a compact patch agrees more
+// often than a 128-pixel row).  The 4 warps of a block take the 4 column classes of one row
+// class; blockIdx.x = 4 * patch column + row class keeps a patch's blocks adjacent, blockIdx.y is
+// the patch row within rows [y0, y1).  MINB: blocks of 128 threads per SM the register budget is
+// sized for.
+__device__ __forceinline__ void patch_pixel(int patch_x, int patch_y, int row_class, int &x, int &y) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    x = patch_x * 32 + 4 * (lane & 7) + w;
+    y = patch_y * 16 + 4 * (lane >> 3) + row_class;
+}
+
 template <int NB, bool F16, bool INF_T, int STEP_MODE, int MINB>
 __global__ void __launch_bounds__(128, MINB) gather_class_kernel(const __grid_constant__ GatherParams P) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int x = blockIdx.x * 128 + 4 * lane + w;
-    const int y = P.y0 + blockIdx.y;
-    if (x >= P.W) return;
+    int x, y;
+    patch_pixel(blockIdx.x >> 2, blockIdx.y, blockIdx.x & 3, x, y);
+    y += P.y0;
+    if (x >= P.W || y >= P.y1) return;
     gather_pixel<NB, F16, INF_T, STEP_MODE>(P, x, y);
 }
 
 // ---------------------------------------------------------------------------------------------
 // Batched form: many frames of different sizes and parameters in one persistent launch.
-// The work list is the concatenation of every frame's tiles (tiles_x = ceil(W/128) tiles per
-// band of `rows` rows, bands top to bottom).  Each block takes the next tile from a queue
+// The work list is the concatenation of every frame's tiles: a tile is `rows` patch rows of one
+// (patch column, row class) pair of the class-strided mapping, tiles_x = 4 ceil(W/32) of them per
+// band of `rows` patch rows, bands top to bottom.  Each block takes the next tile from a queue
 // counter in global memory; tiles are handed out in order, so a block's frame index only moves
 // forward and the frame's parameters are copied to shared memory once per frame change.
 struct FrameDesc {
     GatherParams P;
     int tile_begin;  // global index of the frame's first tile
-    int tiles_x;     // tiles per band
-    int rows;        // rows per tile
+    int tiles_x;     // tiles per band: 4 row classes per 32-pixel patch column
+    int rows;        // patch rows (16 pixel rows each) per tile
     int pad;
 };
 
@@ -559,7 +569,6 @@ __global__ void __launch_bounds__(128, MINB)
     __shared__ GatherParams sP;
     __shared__ int s_tile, s_frame;
     const int n_frames = hdr->n_frames, total = hdr->total_tiles;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int cur = -1;
     for (;;) {
         if (threadIdx.x == 0) {
@@ -583,9 +592,9 @@ __global__ void __launch_bounds__(128, MINB)
         const int local = t - __ldg(&frames[f].tile_begin);
         const int tx = __ldg(&frames[f].tiles_x), rows = __ldg(&frames[f].rows);
         const int band = local / tx, xb = local - band * tx;
-        const int x = xb * 128 + 4 * lane + w;
         for (int r = 0; r < rows; ++r) {
-            const int y = band * rows + r;
+            int x, y;
+            patch_pixel(xb >> 2, band * rows + r, xb & 3, x, y);
             if (y >= sP.H) break;
             if (x < sP.W) gather_pixel<NB, F16, INF_T, STEP_MODE>(sP, x, y);
         }

@@ -11,7 +11,8 @@ cudaError_t launch_single_t(const GatherParams &P, const KernelChoice &k, cudaSt
         dim3 grid((P.W + 31) / 32, (P.y1 - P.y0 + 7) / 8);
         gather_tile_kernel<NB, F16, INF_T, SM><<<grid, 256, 0, s>>>(P);
     } else {
-        dim3 grid((P.W + 127) / 128, P.y1 - P.y0);
+        // 32 x 16 pixel patches, 4 row classes each (see gather_class_kernel)
+        dim3 grid(4 * ((P.W + 31) / 32), (P.y1 - P.y0 + 15) / 16);
         if (k.minb == 8) gather_class_kernel<NB, F16, INF_T, SM, 8><<<grid, 128, 0, s>>>(P);
         else gather_class_kernel<NB, F16, INF_T, SM, 9><<<grid, 128, 0, s>>>(P);
     }
@@ -38,7 +39,7 @@ void single_node_t(const GatherParams &P, const KernelChoice &k, const void **fn
     } else {
         *fn = k.minb == 8 ? reinterpret_cast<const void *>(gather_class_kernel<NB, F16, INF_T, SM, 8>)
                           : reinterpret_cast<const void *>(gather_class_kernel<NB, F16, INF_T, SM, 9>);
-        *grid = dim3((P.W + 127) / 128, P.y1 - P.y0);
+        *grid = dim3(4 * ((P.W + 31) / 32), (P.y1 - P.y0 + 15) / 16);
         *block = dim3(128);
     }
 }

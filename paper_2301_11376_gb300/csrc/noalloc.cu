@@ -95,10 +95,10 @@ extern "C" ssilvb_status ssilvb_gather_batch_noalloc(const ssilvb_frame *frames,
         const ssilvb_frame &f = frames[i];
         std::memset(&fd[i], 0, sizeof(FrameDesc));
         fill_params(fd[i].P, &f.gbuffer, &f.camera, &f.params, &f.out);
-        fd[i].tiles_x = (f.gbuffer.width + 127) / 128;
+        fd[i].tiles_x = 4 * ((f.gbuffer.width + 31) / 32);
         fd[i].rows = k.rows;
         fd[i].tile_begin = (int)tiles;
-        tiles += (long long)fd[i].tiles_x * f.gbuffer.height;
+        tiles += (long long)fd[i].tiles_x * ((f.gbuffer.height + 15) / 16);
     }
     std::memset(hdr, 0, sizeof(BatchHeader));
     hdr->n_frames = n_frames;
