@@ -59,6 +59,7 @@ def _load():
         vp = ctypes.c_void_p
         lib.orc64_pixels.argtypes = [P, ctypes.c_int, vp, vp, vp, vp, vp]
         lib.orc32_pixels.argtypes = [P, ctypes.c_int, vp, vp, vp, vp, vp]
+        lib.orc32_set_trace.argtypes = [vp]
         lib.orc32_acos.argtypes = [ctypes.c_float]
         lib.orc32_acos.restype = ctypes.c_float
         lib.orc32_rsqrt.argtypes = [ctypes.c_float]
@@ -154,6 +155,24 @@ def fp32(prob: Problem, pixels=None, counts: bool = False):
     if counts:
         return o0, o1, m, dict(zip(["pixels", "sky", "slices", "samples", "skipped", "gi_fetches", "ops"], c.tolist()))
     return o0, o1, m
+
+
+def full_path_trace(prob: Problem, pixels) -> np.ndarray:
+    """Which samples of the listed pixels take the full sample path in the binary32 replica (pass
+    the edge-band cosine test): bool [n, N_d, 2 sides, N_s], side -omega first."""
+    xy = _pixels(prob, pixels)
+    n = xy.shape[0]
+    ns = prob.c.steps_per_side
+    tr = np.zeros((n, prob.nd, 2, ns), dtype=np.uint8)
+    lib = _load()
+    lib.orc32_set_trace(tr.ctypes.data)
+    try:
+        rc = lib.orc32_pixels(ctypes.byref(prob.c), n, xy.ctypes.data, None, None, None, None)
+    finally:
+        lib.orc32_set_trace(None)
+    if rc != 0:
+        raise ValueError(f"orc32_pixels rejected the problem (code {rc})")
+    return tr.astype(bool)
 
 
 def acos32(x: float) -> float:

@@ -139,6 +139,9 @@ static int validate(const orc_problem *pb) {
     return 0;
 }
 
+static uint8_t *g_trace = NULL;
+void orc32_set_trace(uint8_t *trace) { g_trace = trace; }
+
 int orc32_pixels(const orc_problem *pb, int n, const int32_t *xy, float *out0, float *out1,
                  uint64_t *masks, int64_t *counts) {
     int bad = validate(pb);
@@ -305,6 +308,7 @@ int orc32_pixels(const orc_problem *pb, int n, const int32_t *xy, float *out0, f
                      * (Section 3.1) the sample occludes nothing, because its back endpoint lies
                      * still closer to that edge. */
                     if (dv * fabsf(dv) < thr2 * ll) continue;
+                    if (g_trace) g_trace[(((size_t)pi * nd + i) * 2 + side) * ns + j] = 1;
                     const float rl = orc32_rsqrt(ll);
                     const float cf = dv * rl;
                     const float Xf = fminf(fmaxf(fmaf(orc32_acos(cf), sK, off), 0.0f), f_nb);
