@@ -56,6 +56,10 @@ SMALL = [
     (40, 30, 18, dict(num_slices=2, steps_per_side=1), True),                  # one step: a pair's second half idle
     (40, 30, 19, dict(num_slices=2, steps_per_side=6, radius=1e6), True),      # projected radius at its 2^20 cap
     (40, 30, 20, dict(num_slices=2, steps_per_side=6, radius=1e-4), True),     # every step on the centre pixel
+    # small radius on a larger frame: most warps take the check-free loop; odd N_s leaves its last
+    # pair's second step idle
+    (200, 150, 23, dict(num_slices=3, steps_per_side=7, radius=0.5), True),
+    (201, 149, 24, dict(num_slices=2, steps_per_side=9, radius=0.4, step_mode=1, sector_count=64), True),
 ]
 
 
