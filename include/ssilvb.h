@@ -198,6 +198,17 @@ ssilvb_status ssilvb_gather_host(ssilvb_ctx *ctx, const ssilvb_gbuffer *gbuffer,
                                  const ssilvb_params *params, const ssilvb_output *out,
                                  struct CUstream_st *stream);
 
+/* ssilvb_gather_host for streams of frames: the same work and results, enqueued on streams the
+ * context owns, and the call returns at once.  Work starts after what is already enqueued on
+ * stream.  Consecutive calls alternate between two staging lanes, so one frame's copies overlap
+ * its neighbours' gathers.  The host buffers of a call must stay valid and unchanged, and its
+ * outputs are complete, only once ssilvb_synchronize(ctx, ...) has returned; that call waits for
+ * every frame enqueued this way.  Errors as ssilvb_gather_host, reported by this call (invalid
+ * arguments, enqueue failures) or by ssilvb_synchronize (execution errors). */
+ssilvb_status ssilvb_gather_host_async(ssilvb_ctx *ctx, const ssilvb_gbuffer *gbuffer,
+                                       const ssilvb_camera *camera, const ssilvb_params *params,
+                                       const ssilvb_output *out, struct CUstream_st *stream);
+
 /* The gather over many frames of uneven sizes in ONE persistent launch (Algorithm 1 per pixel
  * of every frame).  All frames must share sector_count, the storage format of normal and
  * radiance, step_mode, and whether the thickness is infinite (else UNSUPPORTED); every other parameter,
@@ -243,9 +254,10 @@ ssilvb_status ssilvb_gather_batch_noalloc(const ssilvb_frame *frames, int n_fram
 /* Set the context's launch choices for later calls (copied).  INVALID_ARG on an unknown value. */
 ssilvb_status ssilvb_set_tuning(ssilvb_ctx *ctx, const ssilvb_tuning *tuning);
 
-/* Wait for the work enqueued on stream and report a failure of it: CUDA
- * (asynchronous launch or execution error) or DEVICE_CHECK / TIMEOUT from the
- * context's device status word, which the call then clears.  The current kernels
+/* Wait for the work enqueued on stream, and for every frame enqueued by
+ * ssilvb_gather_host_async, and report a failure of it: CUDA (asynchronous launch or
+ * execution error) or DEVICE_CHECK / TIMEOUT from the context's device status word, which
+ * the call then clears.  The current kernels
  * neither wait on the device nor check anything there (every argument is checked on
  * the host before a launch), so those two codes are reserved and never returned. */
 ssilvb_status ssilvb_synchronize(ssilvb_ctx *ctx, struct CUstream_st *stream);

@@ -37,7 +37,7 @@ def _sources():
     return [os.path.join(_CSRC, f) for f in sorted(os.listdir(_CSRC))] + [os.path.join(INCLUDE, "ssilvb.h")]
 
 
-UNITS = ["ssilvb.cu", "batch.cu", "launch_nb32.cu", "launch_nb64.cu", "launch_nb128.cu", "noalloc.cu"]
+UNITS = ["ssilvb.cu", "host.cu", "batch.cu", "launch_nb32.cu", "launch_nb64.cu", "launch_nb128.cu", "noalloc.cu"]
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
@@ -130,7 +130,7 @@ def load():
     lib.ssilvb_create.restype = ctypes.c_int
     lib.ssilvb_destroy.argtypes = [vp]
     lib.ssilvb_destroy.restype = ctypes.c_int
-    for name in ("ssilvb_gather", "ssilvb_gather_host"):
+    for name in ("ssilvb_gather", "ssilvb_gather_host", "ssilvb_gather_host_async"):
         f = getattr(lib, name)
         f.argtypes = [vp, ctypes.POINTER(Gbuffer), ctypes.POINTER(CameraC), ctypes.POINTER(ParamsC),
                       ctypes.POINTER(Output), vp]
@@ -274,10 +274,11 @@ class Context:
                                            ctypes.byref(pc), ctypes.byref(o), ctypes.c_void_p(s.cuda_stream)))
 
     def gather_host(self, depth, normal, radiance, camera, params, out0, out1=None, masks=None, noise=None, sh=None,
-                    stream=None, light_out=None, direct=None):
+                    stream=None, light_out=None, direct=None, asynchronous=False):
         """ssilvb_gather_host on host arrays (numpy or CPU tensors, ideally pinned); synchronous.
         light_out / direct: the multi-bounce light buffer and this frame's direct light, in the
-        radiance format."""
+        radiance format.  asynchronous=True: ssilvb_gather_host_async, which returns at once; the
+        arrays must stay alive and unchanged until synchronize() returns."""
         def ptr(a):
             return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
 
@@ -297,8 +298,9 @@ class Context:
                    ptr(light_out) if light_out is not None else None,
                    pitch(light_out) if light_out is not None else 0)
         sh_ = stream.cuda_stream if stream is not None else None
-        self._check(self.lib.ssilvb_gather_host(self.handle, ctypes.byref(g), ctypes.byref(_camera_c(camera)),
-                                                ctypes.byref(pc), ctypes.byref(o), ctypes.c_void_p(sh_)))
+        fn = self.lib.ssilvb_gather_host_async if asynchronous else self.lib.ssilvb_gather_host
+        self._check(fn(self.handle, ctypes.byref(g), ctypes.byref(_camera_c(camera)), ctypes.byref(pc), ctypes.byref(o),
+                       ctypes.c_void_p(sh_)))
 
     def frame(self, depth, normal, radiance, camera, params, out0, out1=None, masks=None, noise=None, sh=None,
               keep=None):

@@ -18,6 +18,17 @@ namespace ssilvb {
 // ssilvb_gather_host splits a frame into at most this many row bands (one launch each).
 constexpr int kMaxHostBands = 8;
 
+// One host-buffer frame in flight: device staging for its inputs and outputs, the streams its
+// inputs, row bands and output copies run on, and the events that order them.
+struct HostLane {
+    void *stage = nullptr;
+    size_t stage_bytes = 0;
+    cudaStream_t in = nullptr, comp[2] = {nullptr, nullptr}, out = nullptr;
+    cudaEvent_t inputs_ready = nullptr, comp1_done = nullptr, done = nullptr;
+    cudaEvent_t band_done[kMaxHostBands] = {};
+    bool pending = false;  // `done` is recorded and may still be outstanding
+};
+
 // A resolved launch choice.  Every choice gives bit-identical results.
 struct KernelChoice {
     int mapping = SSILVB_MAP_CLASS;  // single frame: SSILVB_MAP_TILE or SSILVB_MAP_CLASS
@@ -88,17 +99,15 @@ struct ssilvb_ctx {
     int num_sms = 0;
     int *d_status = nullptr;  // device status word (device-side checks and bounded waits)
     std::string last_error;
-    void *stage = nullptr;    // staging for ssilvb_gather_host
-    size_t stage_bytes = 0;
-    // ssilvb_gather_host: row bands alternate between the caller's stream and band_stream, and each
-    // band's outputs go back to the host on copy_stream while later bands still compute (created on
-    // first use)
-    cudaStream_t band_stream = nullptr;
-    cudaStream_t copy_stream = nullptr;
-    cudaEvent_t inputs_ready = nullptr;
-    cudaEvent_t band_done[ssilvb::kMaxHostBands] = {};
-    cudaEvent_t bands_done = nullptr;
-    cudaEvent_t copies_done = nullptr;
+    // Host-buffer paths (host.cu), created on first use: the synchronous call's lane borrows the
+    // caller's stream for its inputs and first band stream; the asynchronous calls alternate between
+    // two lanes on context streams, so one frame's copies overlap the next frame's gather.
+    bool host_ready = false;
+    cudaStream_t host_band = nullptr, host_copy = nullptr;               // synchronous lane
+    cudaStream_t async_in = nullptr, async_comp[2] = {}, async_out = nullptr;
+    cudaEvent_t host_entry = nullptr;
+    ssilvb::HostLane sync_lane, async_lane[2];
+    int async_next = 0;
     ssilvb_tuning tuning = {SSILVB_MAP_AUTO, 0, 0, 0, 0, 0, {0, 0}};
     cudaStream_t cap_stream = nullptr;     // private stream the batch graphs are captured on
     std::vector<ssilvb::BatchSlot> slots;  // ring of in-flight batches
@@ -119,6 +128,9 @@ TuneKey tune_key(const ssilvb_gbuffer *g, const ssilvb_params *p, int batch);
 KernelChoice resolve_choice(const ssilvb_ctx *ctx, const TuneKey &key);
 cudaError_t launch_single(const GatherParams &P, int nb, bool f16, bool inf_t, const KernelChoice &k, cudaStream_t s);
 void release_batch_slots(ssilvb_ctx *ctx);
+// Host-buffer paths (host.cu): free their streams, events and staging; wait for asynchronous frames.
+void release_host_resources(ssilvb_ctx *ctx);
+ssilvb_status wait_host_async(ssilvb_ctx *ctx);
 
 struct DeviceGuard {
     int prev = -1;

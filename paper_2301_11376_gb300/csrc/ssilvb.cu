@@ -311,36 +311,14 @@ ssilvb_status ssilvb_create(ssilvb_ctx **out_ctx, int cuda_device) {
     return SSILVB_OK;
 }
 
-// The streams and events of the banded host-buffer path, all or none (a partial set is released).
-static void release_host_streams(ssilvb_ctx *ctx) {
-    for (cudaEvent_t &ev : ctx->band_done)
-        if (ev) cudaEventDestroy(ev), ev = nullptr;
-    for (cudaEvent_t *ev : {&ctx->inputs_ready, &ctx->bands_done, &ctx->copies_done})
-        if (*ev) cudaEventDestroy(*ev), *ev = nullptr;
-    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream), ctx->copy_stream = nullptr;
-    if (ctx->band_stream) cudaStreamDestroy(ctx->band_stream), ctx->band_stream = nullptr;
-}
-
-static cudaError_t create_host_streams(ssilvb_ctx *ctx) {
-    cudaError_t e = cudaStreamCreateWithFlags(&ctx->band_stream, cudaStreamNonBlocking);
-    for (int b = 0; e == cudaSuccess && b < kMaxHostBands; ++b)
-        e = cudaEventCreateWithFlags(&ctx->band_done[b], cudaEventDisableTiming);
-    for (cudaEvent_t *ev : {&ctx->inputs_ready, &ctx->bands_done, &ctx->copies_done})
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking);
-    if (e != cudaSuccess) release_host_streams(ctx);  // copy_stream doubles as the "created" flag
-    return e;
-}
-
 ssilvb_status ssilvb_destroy(ssilvb_ctx *ctx) {
     if (!ctx) return SSILVB_OK;
     DeviceGuard dg(ctx->device);
     cudaDeviceSynchronize();
     if (ctx->d_status) cudaFree(ctx->d_status);
-    if (ctx->stage) cudaFree(ctx->stage);
     release_batch_slots(ctx);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
-    release_host_streams(ctx);
+    release_host_resources(ctx);
     delete ctx;
     return SSILVB_OK;
 }
@@ -358,145 +336,6 @@ ssilvb_status ssilvb_gather(ssilvb_ctx *ctx, const ssilvb_gbuffer *gbuffer, cons
     cudaError_t e = launch_single(P, params->sector_count, gbuffer->normal_fmt == SSILVB_FMT_F16X4,
                                   std::isinf(params->thickness), k, reinterpret_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "gather launch");
-    return SSILVB_OK;
-}
-
-ssilvb_status ssilvb_gather_host(ssilvb_ctx *ctx, const ssilvb_gbuffer *gbuffer, const ssilvb_camera *camera,
-                                 const ssilvb_params *params, const ssilvb_output *out,
-                                 struct CUstream_st *stream) {
-    if (!ctx) return fail(nullptr, SSILVB_ERR_INVALID_ARG, "ctx is NULL");
-    ctx->last_error.clear();
-    DeviceGuard dg(ctx->device);
-    ssilvb_status s = validate(ctx, gbuffer, camera, params, out, false);
-    if (s != SSILVB_OK) return s;
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    const size_t W = gbuffer->width, H = gbuffer->height;
-    const size_t px = gbuffer->normal_fmt == SSILVB_FMT_F16X4 ? 8 : 16;
-    const int na = params->ambient_cones;
-    const size_t mask_bytes = out->masks ? (size_t)params->num_slices * W * H * (params->sector_count / 8) : 0;
-    auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
-    const size_t b_depth = up(W * H * 4), b_px = up(W * H * px), b_out = up(W * H * 16);
-    const size_t b_light = out->light_out ? up(W * H * px) : 0;
-    const size_t b_direct = (out->light_out && gbuffer->direct) ? up(W * H * px) : 0;
-    const size_t need = b_depth + 2 * b_px + b_out + (na > 0 ? b_out : 0) + up(mask_bytes) + b_light + b_direct;
-    if (need > ctx->stage_bytes) {
-        if (ctx->stage) {
-            cudaError_t e = cudaStreamSynchronize(st);
-            if (e != cudaSuccess) return cuda_fail(ctx, e, "stream synchronize");
-            cudaFree(ctx->stage);
-            ctx->stage = nullptr;
-            ctx->stage_bytes = 0;
-        }
-        cudaError_t e = cudaMalloc(&ctx->stage, need);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return fail(ctx, SSILVB_ERR_OUT_OF_MEMORY, "staging allocation of %zu bytes failed", need);
-        }
-        ctx->stage_bytes = need;
-    }
-    char *base = static_cast<char *>(ctx->stage);
-    float *d_depth = reinterpret_cast<float *>(base);
-    char *d_normal = base + b_depth;
-    char *d_rad = d_normal + b_px;
-    float *d_out0 = reinterpret_cast<float *>(d_rad + b_px);
-    float *d_out1 = na > 0 ? reinterpret_cast<float *>(reinterpret_cast<char *>(d_out0) + b_out) : nullptr;
-    void *d_masks = out->masks ? reinterpret_cast<char *>(d_out0) + b_out + (na > 0 ? b_out : 0) : nullptr;
-    void *d_light = out->light_out ? reinterpret_cast<char *>(d_out0) + b_out + (na > 0 ? b_out : 0) + up(mask_bytes)
-                                   : nullptr;
-    void *d_direct = b_direct ? reinterpret_cast<char *>(d_out0) + b_out + (na > 0 ? b_out : 0) + up(mask_bytes) +
-                                    b_light
-                              : nullptr;
-
-    cudaError_t e = cudaMemcpy2DAsync(d_depth, W * 4, gbuffer->depth, gbuffer->depth_pitch, W * 4, H,
-                                      cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess)
-        e = cudaMemcpy2DAsync(d_normal, W * px, gbuffer->normal, gbuffer->normal_pitch, W * px, H,
-                              cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess)
-        e = cudaMemcpy2DAsync(d_rad, W * px, gbuffer->radiance, gbuffer->radiance_pitch, W * px, H,
-                              cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && d_direct)
-        e = cudaMemcpy2DAsync(d_direct, W * px, gbuffer->direct, gbuffer->direct_pitch, W * px, H,
-                              cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "host-to-device copy");
-
-    ssilvb_gbuffer dg_ = *gbuffer;
-    dg_.direct = d_direct;
-    dg_.direct_pitch = d_direct ? W * px : 0;
-    dg_.depth = d_depth;
-    dg_.depth_pitch = W * 4;
-    dg_.normal = d_normal;
-    dg_.normal_pitch = W * px;
-    dg_.radiance = d_rad;
-    dg_.radiance_pitch = W * px;
-    ssilvb_output dout = {d_out0, W * 16, d_out1, W * 16, d_masks, d_light, W * px};
-    ssilvb::GatherParams P;
-    fill_params(P, &dg_, camera, params, &dout);
-    const KernelChoice k = resolve_choice(ctx, tune_key(gbuffer, params, 0));
-    if (!ctx->copy_stream) {
-        e = create_host_streams(ctx);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "copy stream set-up");
-    }
-    // Row bands, one launch each, for frames of 512+ rows.  Every band reads the whole frame's
-    // inputs, so the inputs go first; then band b's outputs go back on the copy stream while later
-    // bands compute.  Bands alternate between two streams, so that one band's last wave overlaps
-    // the next band's first instead of draining the GPU between launches.  Band b gets a share of
-    // the rows proportional to 10 - b: the last band, whose copy nothing hides, is the smallest.
-    const int bands = (int)std::max<size_t>(1, std::min<size_t>(kMaxHostBands, H / 256));
-    size_t cut[kMaxHostBands + 1] = {0};
-    {
-        size_t wsum = 0, w = 0;
-        for (int b = 0; b < bands; ++b) wsum += 10 - b;
-        for (int b = 0; b < bands; ++b) {
-            w += 10 - b;
-            cut[b + 1] = H * w / wsum;
-        }
-    }
-    const size_t melem = params->sector_count / 8;
-    cudaStream_t cs = ctx->copy_stream;
-    e = cudaEventRecord(ctx->inputs_ready, st);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->band_stream, ctx->inputs_ready, 0);
-    for (int b = 0; b < bands && e == cudaSuccess; ++b) {
-        const size_t y0 = cut[b], y1 = cut[b + 1], n = y1 - y0;
-        cudaStream_t ls = (b & 1) ? ctx->band_stream : st;
-        P.y0 = (int)y0;
-        P.y1 = (int)y1;
-        e = launch_single(P, params->sector_count, gbuffer->normal_fmt == SSILVB_FMT_F16X4,
-                          std::isinf(params->thickness), k, ls);
-        if (e != cudaSuccess) break;
-        e = cudaEventRecord(ctx->band_done[b], ls);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ctx->band_done[b], 0);
-        if (e == cudaSuccess)
-            e = cudaMemcpy2DAsync(reinterpret_cast<char *>(out->out0) + y0 * out->out0_pitch, out->out0_pitch,
-                                  reinterpret_cast<char *>(d_out0) + y0 * W * 16, W * 16, W * 16, n,
-                                  cudaMemcpyDeviceToHost, cs);
-        if (e == cudaSuccess && na > 0)
-            e = cudaMemcpy2DAsync(reinterpret_cast<char *>(out->out1) + y0 * out->out1_pitch, out->out1_pitch,
-                                  reinterpret_cast<char *>(d_out1) + y0 * W * 16, W * 16, W * 16, n,
-                                  cudaMemcpyDeviceToHost, cs);
-        for (int i = 0; e == cudaSuccess && out->masks && i < params->num_slices; ++i) {
-            const size_t o = ((size_t)i * H + y0) * W * melem;  // [N_d][H][W] words: rows y0..y1 of slice i
-            e = cudaMemcpyAsync(static_cast<char *>(out->masks) + o, static_cast<char *>(d_masks) + o, n * W * melem,
-                                cudaMemcpyDeviceToHost, cs);
-        }
-        if (e == cudaSuccess && out->light_out)
-            e = cudaMemcpy2DAsync(static_cast<char *>(out->light_out) + y0 * out->light_out_pitch,
-                                  out->light_out_pitch, static_cast<char *>(d_light) + y0 * W * px, W * px, W * px, n,
-                                  cudaMemcpyDeviceToHost, cs);
-    }
-    if (e == cudaSuccess) e = cudaEventRecord(ctx->bands_done, ctx->band_stream);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->bands_done, 0);
-    if (e == cudaSuccess) e = cudaEventRecord(ctx->copies_done, cs);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->copies_done, 0);
-    if (e != cudaSuccess) {
-        // nothing enqueued so far may still write into the caller's buffers after the return
-        cudaStreamSynchronize(ctx->band_stream);
-        cudaStreamSynchronize(cs);
-        cudaStreamSynchronize(st);
-        return cuda_fail(ctx, e, "banded gather or device-to-host copy");
-    }
-    e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "gather execution");
     return SSILVB_OK;
 }
 
@@ -526,6 +365,8 @@ ssilvb_status ssilvb_synchronize(ssilvb_ctx *ctx, struct CUstream_st *stream) {
     DeviceGuard dg(ctx->device);
     cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "stream execution");
+    const ssilvb_status hs = wait_host_async(ctx);
+    if (hs != SSILVB_OK) return hs;
     int st = 0;
     e = cudaMemcpy(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "status read");

@@ -219,6 +219,36 @@ def test_host_buffers_in_row_bands(ctx, f16):
     assert np.abs(lo[..., :3].astype(np.float64)).max() > 0
 
 
+def test_host_buffers_asynchronous_stream_of_frames(ctx):
+    """ssilvb_gather_host_async: frames of growing size enqueued back to back (two staging lanes,
+    one frame's copies overlapping the next frame's gather, staging grown between uses) equal the
+    synchronous call frame by frame, bit for bit, also when synchronous calls are interleaved."""
+    prm = Params(num_slices=2, steps_per_side=8, sector_count=64, ambient_cones=4)
+    noise, sh = scenegen.ign_table(), scenegen.sh_environment(7)
+    frames = [scenegen.render(40 + k, 64 + 16 * k, 520 + 40 * k, 8, 3) for k in range(5)]
+
+    def outputs(g):
+        H, W = g.depth.shape
+        return (np.zeros((H, W, 4), np.float32), np.zeros((H, W, 4), np.float32),
+                np.zeros((prm.num_slices, H, W), np.uint64))
+
+    expected = []
+    for g in frames:
+        o = outputs(g)
+        ctx.gather_host(g.depth, g.normal, g.radiance, g.camera, prm, *o, noise=noise, sh=sh)
+        expected.append(o)
+    got = [outputs(g) for g in frames]
+    for k, (g, o) in enumerate(zip(frames, got)):
+        if k == 2:  # a synchronous call in the middle of the stream
+            ctx.gather_host(g.depth, g.normal, g.radiance, g.camera, prm, *o, noise=noise, sh=sh)
+        else:
+            ctx.gather_host(g.depth, g.normal, g.radiance, g.camera, prm, *o, noise=noise, sh=sh, asynchronous=True)
+    ctx.synchronize()
+    for k, (a, b) in enumerate(zip(expected, got)):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y), k
+
+
 def test_invalid_arguments_enqueue_nothing(ctx):
     import torch
 
