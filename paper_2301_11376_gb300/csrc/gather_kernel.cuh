@@ -284,37 +284,44 @@ struct Pixel {
 // The rest of one sample of side POS (+omega when true) once its front cosine lies outside the
 // side's edge band: front and back endpoints, sector run, mask update and indirect light.
 // (lx, ly, lz) = l = s_f - p, dv = l.v, ll = |l|^2; (qx, qy) the sample pixel.
-template <int NB, bool F16, bool INF_T, bool POS>
-__device__ __forceinline__ void full_step(const GatherParams &P, const Pixel &X, float lx, float ly, float lz, float dv,
-                                          float ll, int qx, int qy, float off, typename MaskT<NB>::T &b,
-                                          float &GIr, float &GIg, float &GIb) {
-    using M = typename MaskT<NB>::T;
+// Sector coordinates of a sample's front and back endpoints, and 1/|l|, for a sample outside the
+// cosine band; false when its front endpoint still lies in the band in sector units (half a sector
+// for the half-covered rule, the edge for floor/ceil), so that it occludes nothing.  The back sample
+// lies thickness t behind the front one along the centre pixel's view ray; t = infinity puts the
+// back endpoint on the side's hemisphere edge.  Both angles are one packed pair: a sample outside
+// the cosine band almost always needs both.
+template <bool INF_T, bool POS>
+__device__ __forceinline__ bool endpoints(const GatherParams &P, const Pixel &X, float dv, float ll, float off,
+                                          float &rl, float &Xf, float &Xb) {
     const float sK = POS ? P.K : -P.K;
-    float rl, Xf, Xb;
     if (!INF_T) {
-        // Back sample, thickness t behind the front one along the centre pixel's view ray; both
-        // endpoint angles as one pair (a sample outside the cosine band almost always needs both).
         const float dvb = dv - X.tp;
         const float llb = fmaf(X.m2t, dv, ll + X.t2);
         const float2 r2 = own_rsqrt_pair(make_float2(ll, llb));
         rl = r2.x;
         const float2 e2 = pfma(own_acos_pair(pmul(make_float2(dv, dvb), r2)), bcast(sK), bcast(off));
         Xf = fminf(fmaxf(e2.x, 0.0f), P.f_nb);
-        // the same band in sector units (half a sector for the half-covered rule, the edge for floor/ceil)
-        if (POS ? Xf > P.edge_hi : Xf < P.edge_lo) return;
         Xb = fminf(fmaxf(e2.y, 0.0f), P.f_nb);
     } else {
         rl = own_rsqrt(ll);
         Xf = fminf(fmaxf(fmaf(own_acos(dv * rl), sK, off), 0.0f), P.f_nb);
-        if (POS ? Xf > P.edge_hi : Xf < P.edge_lo) return;
         Xb = POS ? P.f_nb : 0.0f;
     }
-    // [A, B]: the back endpoint lies toward this side's edge (a rounding-level reversal gives B < A).
+    return !(POS ? Xf > P.edge_hi : Xf < P.edge_lo);
+}
+
+// Sector run [A, B] (the back endpoint lies toward this side's edge; a rounding-level reversal gives
+// B < A and no sector), mask update, and the indirect light of the newly occluded sectors
+// (Section 3.3).
+template <int NB, bool F16, bool POS>
+__device__ __forceinline__ void occlude(const GatherParams &P, const Pixel &X, float lx, float ly, float lz, float rl,
+                                        float Xf, float Xb, int qx, int qy, typename MaskT<NB>::T &b, float &GIr,
+                                        float &GIg, float &GIb) {
+    using M = typename MaskT<NB>::T;
     const float A = POS ? Xf : Xb, B = POS ? Xb : Xf;
     const M bj = sector_run<NB>(A, B, P.hit_rule);
     const int newly = popc_(bj & ~b);
     b |= bj;
-    // Indirect light of the newly occluded sectors (Section 3.3).
     if (newly > 0 && P.gi) {
         const float3 cj = load_xyz<F16>(P.radiance, P.radiance_pitch, qx, qy);
         const float3 nj = load_xyz<F16>(P.normal, P.normal_pitch, qx, qy);
@@ -324,6 +331,25 @@ __device__ __forceinline__ void full_step(const GatherParams &P, const Pixel &X,
         GIr = fmaf(wgt, cj.x, GIr);
         GIg = fmaf(wgt, cj.y, GIg);
         GIb = fmaf(wgt, cj.z, GIb);
+    }
+}
+
+// The rest of a step pair's samples that left the cosine band (fa / fb): endpoints, then the mask
+// and indirect light, sample j before sample j + 1.
+template <int NB, bool F16, bool INF_T, bool POS>
+__device__ __forceinline__ void pair_full(const GatherParams &P, const Pixel &X, bool fa, bool fb, float2 lx,
+                                          float2 ly, float2 lz, float2 dv, float2 ll, int qxa, int qya, int qxb,
+                                          int qyb, float off, typename MaskT<NB>::T &b, float &GIr, float &GIg,
+                                          float &GIb) {
+    if (fa) {
+        float rl, Xf, Xb;
+        if (endpoints<INF_T, POS>(P, X, dv.x, ll.x, off, rl, Xf, Xb))
+            occlude<NB, F16, POS>(P, X, lx.x, ly.x, lz.x, rl, Xf, Xb, qxa, qya, b, GIr, GIg, GIb);
+    }
+    if (fb) {
+        float rl, Xf, Xb;
+        if (endpoints<INF_T, POS>(P, X, dv.y, ll.y, off, rl, Xf, Xb))
+            occlude<NB, F16, POS>(P, X, lx.y, ly.y, lz.y, rl, Xf, Xb, qxb, qyb, b, GIr, GIg, GIb);
     }
 }
 
@@ -383,10 +409,9 @@ __device__ __forceinline__ void march_side(const GatherParams &P, const Pixel &X
                 const float2 dv = pfma(lx, bcast(X.vx), pfma(ly, bcast(X.vy), pmul(lz, bcast(X.vz))));
                 const float2 ll = pfma(lx, lx, pfma(ly, ly, pmul(lz, lz)));
                 const float2 lim = pmul(bcast(thr2), ll);
-                if (is_geometry(za) && !(dv.x * fabsf(dv.x) < lim.x))
-                    full_step<NB, F16, INF_T, POS>(P, X, lx.x, ly.x, lz.x, dv.x, ll.x, qxa, qya, off, b, GIr, GIg, GIb);
-                if (is_geometry(zb) && !(dv.y * fabsf(dv.y) < lim.y))
-                    full_step<NB, F16, INF_T, POS>(P, X, lx.y, ly.y, lz.y, dv.y, ll.y, qxb, qyb, off, b, GIr, GIg, GIb);
+                pair_full<NB, F16, INF_T, POS>(P, X, is_geometry(za) && !(dv.x * fabsf(dv.x) < lim.x),
+                                               is_geometry(zb) && !(dv.y * fabsf(dv.y) < lim.y), lx, ly, lz, dv, ll,
+                                               qxa, qya, qxb, qyb, off, b, GIr, GIg, GIb);
             }
             return;
         }
@@ -427,11 +452,10 @@ __device__ __forceinline__ void march_side(const GatherParams &P, const Pixel &X
         // through the monotone map x -> x |x|) the back endpoint lies still closer to the edge, so
         // no sector is half covered.
         const float2 lim = pmul(bcast(thr2), ll);
-        if (is_geometry(za) && !(dv.x * fabsf(dv.x) < lim.x))
-            full_step<NB, F16, INF_T, POS>(P, X, lx.x, ly.x, lz.x, dv.x, ll.x, qxa, qya, off, b, GIr, GIg, GIb);
+        pair_full<NB, F16, INF_T, POS>(P, X, is_geometry(za) && !(dv.x * fabsf(dv.x) < lim.x),
+                                       onb && is_geometry(zb) && !(dv.y * fabsf(dv.y) < lim.y), lx, ly, lz, dv, ll,
+                                       qxa, qya, qxb, qyb, off, b, GIr, GIg, GIb);
         if (!onb) break;
-        if (is_geometry(zb) && !(dv.y * fabsf(dv.y) < lim.y))
-            full_step<NB, F16, INF_T, POS>(P, X, lx.y, ly.y, lz.y, dv.y, ll.y, qxb, qyb, off, b, GIr, GIg, GIb);
     }
 }
 
