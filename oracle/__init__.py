@@ -157,9 +157,10 @@ def fp32(prob: Problem, pixels=None, counts: bool = False):
     return o0, o1, m
 
 
-def full_path_trace(prob: Problem, pixels) -> np.ndarray:
-    """Which samples of the listed pixels take the full sample path in the binary32 replica (pass
-    the edge-band cosine test): bool [n, N_d, 2 sides, N_s], side -omega first."""
+def sample_trace(prob: Problem, pixels) -> np.ndarray:
+    """Per-sample decisions of the binary32 replica on the listed pixels: uint8 [n, N_d, 2 sides, N_s],
+    side -omega first; bit 0: the sample passes the edge-band cosine test (full sample path),
+    bit 1: it also newly occludes a sector (indirect light)."""
     xy = _pixels(prob, pixels)
     n = xy.shape[0]
     ns = prob.c.steps_per_side
@@ -172,7 +173,12 @@ def full_path_trace(prob: Problem, pixels) -> np.ndarray:
         lib.orc32_set_trace(None)
     if rc != 0:
         raise ValueError(f"orc32_pixels rejected the problem (code {rc})")
-    return tr.astype(bool)
+    return tr
+
+
+def full_path_trace(prob: Problem, pixels) -> np.ndarray:
+    """Which samples take the full sample path in the binary32 replica: bool [n, N_d, 2, N_s]."""
+    return (sample_trace(prob, pixels) & 1).astype(bool)
 
 
 def acos32(x: float) -> float:

@@ -56,9 +56,9 @@ int orc32_pixels(const orc_problem *pb, int n, const int32_t *xy, float *out0, f
                  uint64_t *masks, int64_t *counts);
 
 /* Optional per-sample trace of the next orc32_pixels calls (NULL turns it off): one byte per
- * (pixel, slice, side, step), laid out [n][N_d][2][N_s], set to 1 where the sample passes the
- * edge-band cosine test and so takes the full sample path; the caller zeroes it.  Used by the
- * warp-layout study in tests. */
+ * (pixel, slice, side, step), laid out [n][N_d][2][N_s]: bit 0 where the sample passes the
+ * edge-band cosine test and so takes the full sample path, bit 1 where it also newly occludes a
+ * sector and adds indirect light; the caller zeroes it.  Used by the warp-layout study in tests. */
 void orc32_set_trace(uint8_t *trace);
 
 /* The replica's own arccosine (Abramowitz and Stegun 4.4.46 in binary32), exposed for tests. */

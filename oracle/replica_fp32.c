@@ -308,7 +308,8 @@ int orc32_pixels(const orc_problem *pb, int n, const int32_t *xy, float *out0, f
                      * (Section 3.1) the sample occludes nothing, because its back endpoint lies
                      * still closer to that edge. */
                     if (dv * fabsf(dv) < thr2 * ll) continue;
-                    if (g_trace) g_trace[(((size_t)pi * nd + i) * 2 + side) * ns + j] = 1;
+                    uint8_t *tr = g_trace ? g_trace + (((size_t)pi * nd + i) * 2 + side) * ns + j : NULL;
+                    if (tr) *tr = 1;
                     const float rl = orc32_rsqrt(ll);
                     const float cf = dv * rl;
                     const float Xf = fminf(fmaxf(fmaf(orc32_acos(cf), sK, off), 0.0f), f_nb);
@@ -338,6 +339,7 @@ int orc32_pixels(const orc_problem *pb, int n, const int32_t *xy, float *out0, f
                     /* Indirect light from the newly occluded sectors (Section 3.3). */
                     if (newly > 0 && pb->gi) {
                         ++c_gi;
+                        if (tr) *tr |= 2;
                         const float *cj = pb->radiance + 4 * q, *nj = pb->normal + 4 * q;
                         const float cp = fmaxf(fmaf(nx, lx, fmaf(ny, ly, nz * lz)) * rl, 0.0f);
                         const float cq = fmaxf(-(fmaf(nj[0], lx, fmaf(nj[1], ly, nj[2] * lz)) * rl), 0.0f);
