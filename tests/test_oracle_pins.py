@@ -201,9 +201,12 @@ def test_step_wall_closed_form(thickness, axis):
 
 # --- single sample: closed-form indirect light (Algorithm 1 GI line, Section 3.3) -------------
 
-def test_single_sample_gi_closed_form():
-    """Sky everywhere except the centre pixel p and one pixel q on the first step of the
-    +omega side of slice 0.  The result is that sample alone: cnt sectors of its slab,
+@pytest.mark.parametrize("step_mode,step", [(0, 0), (1, 2)])
+def test_single_sample_gi_closed_form(step_mode, step):
+    """Sky everywhere except the centre pixel p and one pixel q on step `step` of the +omega
+    side of slice 0 (constant steps, or quadratic steps r ((j+1)/(N_s+1))^2: the reading taken of
+    the growing step lengths of Section 4.3).
+    The result is that sample alone: cnt sectors of its slab,
     GI = cnt/N_b * c_q * max(0, n_p.l) * max(0, -n_q.l) / N_d."""
     W = H = 31
     fx = 15.5
@@ -211,8 +214,9 @@ def test_single_sample_gi_closed_form():
     c = 15
     radius, ns, nb, t = 2.0, 4, 32, 0.4
     z, zq = 3.0, 2.2
-    offs = G.sample_offsets(radius, fx, z, ns)
-    dq = int(np.rint(offs[0]))
+    offs = G.sample_offsets(radius, fx, z, ns, step_mode=step_mode)
+    dq = int(np.rint(offs[step]))
+    assert dq >= 1 and all(int(np.rint(o)) != dq for k, o in enumerate(offs) if k != step)
     depth = np.full((H, W), np.inf, dtype=np.float32)
     depth[c, c] = z
     depth[c, c + dq] = zq
@@ -224,7 +228,7 @@ def test_single_sample_gi_closed_form():
     cq = np.array([0.9, 0.4, 0.2], dtype=np.float32)
     rad[c, c + dq, :3] = cq
     g = scenegen.GBuffer(depth, nrm, rad, cam)
-    prm = Params(num_slices=1, steps_per_side=ns, radius=radius, thickness=t, sector_count=nb)
+    prm = Params(num_slices=1, steps_per_side=ns, radius=radius, thickness=t, sector_count=nb, step_mode=step_mode)
 
     # closed form
     n_p = np.array([0.0, 0.0, 1.0])
