@@ -56,12 +56,14 @@ def make_workload(name, nb):
     return scenegen.workload_256()
 
 
-KERNEL_SOURCES = ["gather_kernel.cuh", "launch_impl.cuh", "launch_nb32.cu", "launch_nb64.cu", "launch_nb128.cu"]
+KERNEL_SOURCES = ["gather_kernel.cuh", "launch_impl.cuh", "launch_nb32.cu", "launch_nb64.cu", "launch_nb128.cu",
+                  "internal.h"]  # internal.h: the default launch choice (blocks per SM)
 
 
 def kernel_sources_sha256():
-    """Hash of the device code (the kernel and its instantiating units) and the nvcc flags:
-    measured DRAM counters apply only to this code; host-side changes leave them valid."""
+    """Hash of the device code (the kernel, its instantiating units and the default launch
+    choice) and the nvcc flags: measured DRAM counters apply only to this code; other host-side
+    changes leave them valid."""
     import hashlib
 
     import paper_2301_11376_gb300 as ssilvb

@@ -341,6 +341,7 @@ __device__ __forceinline__ void pair_full(const GatherParams &P, const Pixel &X,
                                           float2 ly, float2 lz, float2 dv, float2 ll, int qxa, int qya, int qxb,
                                           int qyb, float off, typename MaskT<NB>::T &b, float &GIr, float &GIg,
                                           float &GIb) {
+    if (!(fa | fb)) return;  // the common case: one branch for the pair
     if (fa) {
         float rl, Xf, Xb;
         if (endpoints<INF_T, POS>(P, X, dv.x, ll.x, off, rl, Xf, Xb))
@@ -364,60 +365,81 @@ __device__ __forceinline__ void march_side(const GatherParams &P, const Pixel &X
                                            float sphi, float off, float thr2,
                                            typename MaskT<NB>::T &b, float &GIr, float &GIg, float &GIb) {
     const float wsx = POS ? cphi : -cphi, wsy = POS ? sphi : -sphi;
+    int j0 = 0;
     {
-        // The offsets grow with j, so the last step's offset bounds every step's pixel offset
-        // (|round(o w)| <= o_last |w| + 1/2), and if the first step is off the centre pixel so are
-        // the rest.  When that holds for every active lane, the side runs in the loop below
-        // without the per-step screen and centre tests.  (A copy of the checked loop that
-        // follows rather than a template parameter of one loop: the shared form compiled to
-        // 3 % slower code.)
-        float o_last, o_first;
+        // Steps 0 .. J-1 provably stay on screen when the offset of step J-1 does (offsets grow with
+        // j), which holds when ceil(o |w| + 1) is within the pixels left to the screen edge in this
+        // side's direction along each axis (|round(o w)| <= o |w| + 1/2); and if the first step is
+        // off the centre pixel so are the rest.  Each lane estimates its J from the inverse of the
+        // offset formula, then confirms it with that exact bound, stepping back at most twice.  The
+        // warp runs the smallest J (in whole step pairs) without the per-step screen and centre
+        // tests, then the remaining steps with them.  (A copy of the checked loop rather than a
+        // template parameter of one loop: the shared form compiled to 3 % slower code.)
+        float o_first;
         if (STEP_MODE == 0) {
-            o_last = fmaf((float)P.ns, X.del, X.xdel);
             o_first = fmaf(1.0f, X.del, X.xdel);
         } else {
-            const float ul = fmaf((float)P.ns, X.dn_, X.xidn), uf = fmaf(1.0f, X.dn_, X.xidn);
-            o_last = (ul * ul) * X.rpx;
+            const float uf = fmaf(1.0f, X.dn_, X.xidn);
             o_first = (uf * uf) * X.rpx;
         }
-        const int bx = __float2int_ru(fmaf(o_last, fabsf(wsx), 1.0f));
-        const int by = __float2int_ru(fmaf(o_last, fabsf(wsy), 1.0f));
         const bool off_centre = (fmaf(o_first, wsx, kMagic) != kMagic) | (fmaf(o_first, wsy, kMagic) != kMagic);
-        const bool inside = off_centre && bx <= x && x <= P.W - 1 - bx && by <= y && y <= P.H - 1 - by;
-        if (__all_sync(__activemask(), inside)) {
-            for (int j = 0; j < P.ns; j += 2) {
-                const float2 jf = make_float2((float)(j + 1), (float)(j + 2));
-                float2 o;
+        int J = 0;
+        if (off_centre) {
+            const float ax = fabsf(wsx), ay = fabsf(wsy);
+            const int dxi = wsx >= 0.0f ? P.W - 1 - x : x, dyi = wsy >= 0.0f ? P.H - 1 - y : y;
+            const float t = fminf(((float)dxi - 1.0f) / ax, ((float)dyi - 1.0f) / ay);
+            const float jm = STEP_MODE == 0 ? (t - X.xdel) / X.del
+                                            : (sqrtf(fmaxf(t, 0.0f) / X.rpx) - X.xidn) / X.dn_;
+            J = (int)fminf(fmaxf(floorf(jm), 0.0f), (float)P.ns);
+            auto fits = [&](int n) {  // step n - 1 (and so every earlier step) on screen
+                float o;
                 if (STEP_MODE == 0) {
-                    o = pfma(jf, bcast(X.del), bcast(X.xdel));
+                    o = fmaf((float)n, X.del, X.xdel);
                 } else {
-                    const float2 uj = pfma(jf, bcast(X.dn_), bcast(X.xidn));
-                    o = pmul(pmul(uj, uj), bcast(X.rpx));
+                    const float u = fmaf((float)n, X.dn_, X.xidn);
+                    o = (u * u) * X.rpx;
                 }
-                const float2 rx = pfma(o, bcast(wsx), bcast(kMagic)), ry = pfma(o, bcast(wsy), bcast(kMagic));
-                const int qxa = __float_as_int(rx.x) + X.qx0, qya = __float_as_int(ry.x) + X.qy0;
-                const int qxb = __float_as_int(rx.y) + X.qx0, qyb = __float_as_int(ry.y) + X.qy0;
-                const bool onb = j + 1 < P.ns;
-                const float za = __ldg(P.depth + (unsigned)qya * (unsigned)P.depth_pitch + (unsigned)qxa);
-                float zb = 0.0f;
-                if (onb) zb = __ldg(P.depth + (unsigned)qyb * (unsigned)P.depth_pitch + (unsigned)qxb);
-                const float2 dxf = psub(rx, bcast(kMagic)), dyf = psub(ry, bcast(kMagic));
-                const float2 aq = pfma(dxf, bcast(P.inv_fx), bcast(X.ax)), bq = pfma(dyf, bcast(P.ninv_fy), bcast(X.by));
-                const float2 zq = make_float2(za, zb);
-                const float2 lx = pfma(aq, zq, bcast(-X.px)), ly = pfma(bq, zq, bcast(-X.py));
-                const float2 lz = psub(bcast(X.z), zq);
-                const float2 dv = pfma(lx, bcast(X.vx), pfma(ly, bcast(X.vy), pmul(lz, bcast(X.vz))));
-                const float2 ll = pfma(lx, lx, pfma(ly, ly, pmul(lz, lz)));
-                const float2 lim = pmul(bcast(thr2), ll);
-                pair_full<NB, F16, INF_T, POS>(P, X, is_geometry(za) && !(dv.x * fabsf(dv.x) < lim.x),
-                                               is_geometry(zb) && !(dv.y * fabsf(dv.y) < lim.y), lx, ly, lz, dv, ll,
-                                               qxa, qya, qxb, qyb, off, b, GIr, GIg, GIb);
+                return __float2int_ru(fmaf(o, ax, 1.0f)) <= dxi && __float2int_ru(fmaf(o, ay, 1.0f)) <= dyi;
+            };
+            if (J > 0 && !fits(J)) {
+                --J;
+                if (J > 0 && !fits(J)) J = 0;
             }
-            return;
         }
+        const int Jw = __reduce_min_sync(__activemask(), J);
+        j0 = Jw >= P.ns ? P.ns : (Jw & ~1);
+        for (int j = 0; j < j0; j += 2) {
+            const float2 jf = make_float2((float)(j + 1), (float)(j + 2));
+            float2 o;
+            if (STEP_MODE == 0) {
+                o = pfma(jf, bcast(X.del), bcast(X.xdel));
+            } else {
+                const float2 uj = pfma(jf, bcast(X.dn_), bcast(X.xidn));
+                o = pmul(pmul(uj, uj), bcast(X.rpx));
+            }
+            const float2 rx = pfma(o, bcast(wsx), bcast(kMagic)), ry = pfma(o, bcast(wsy), bcast(kMagic));
+            const int qxa = __float_as_int(rx.x) + X.qx0, qya = __float_as_int(ry.x) + X.qy0;
+            const int qxb = __float_as_int(rx.y) + X.qx0, qyb = __float_as_int(ry.y) + X.qy0;
+            const bool onb = j + 1 < P.ns;  // false only for the last step of an odd N_s
+            const float za = __ldg(P.depth + (unsigned)qya * (unsigned)P.depth_pitch + (unsigned)qxa);
+            float zb = 0.0f;
+            if (onb) zb = __ldg(P.depth + (unsigned)qyb * (unsigned)P.depth_pitch + (unsigned)qxb);
+            const float2 dxf = psub(rx, bcast(kMagic)), dyf = psub(ry, bcast(kMagic));
+            const float2 aq = pfma(dxf, bcast(P.inv_fx), bcast(X.ax)), bq = pfma(dyf, bcast(P.ninv_fy), bcast(X.by));
+            const float2 zq = make_float2(za, zb);
+            const float2 lx = pfma(aq, zq, bcast(-X.px)), ly = pfma(bq, zq, bcast(-X.py));
+            const float2 lz = psub(bcast(X.z), zq);
+            const float2 dv = pfma(lx, bcast(X.vx), pfma(ly, bcast(X.vy), pmul(lz, bcast(X.vz))));
+            const float2 ll = pfma(lx, lx, pfma(ly, ly, pmul(lz, lz)));
+            const float2 lim = pmul(bcast(thr2), ll);
+            pair_full<NB, F16, INF_T, POS>(P, X, is_geometry(za) && !(dv.x * fabsf(dv.x) < lim.x),
+                                           is_geometry(zb) && !(dv.y * fabsf(dv.y) < lim.y), lx, ly, lz, dv, ll,
+                                           qxa, qya, qxb, qyb, off, b, GIr, GIg, GIb);
+        }
+        if (j0 >= P.ns) return;
     }
 
-    for (int j = 0; j < P.ns; j += 2) {
+    for (int j = j0; j < P.ns; j += 2) {
         // offsets r (j + 1 + xi_s)/(N_s + 1), or the quadratic form, of steps j and j + 1
         const float2 jf = make_float2((float)(j + 1), (float)(j + 2));
         float2 o;

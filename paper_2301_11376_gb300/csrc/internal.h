@@ -32,7 +32,7 @@ struct HostLane {
 // A resolved launch choice.  Every choice gives bit-identical results.
 struct KernelChoice {
     int mapping = SSILVB_MAP_CLASS;  // single frame: SSILVB_MAP_TILE or SSILVB_MAP_CLASS
-    int minb = 8;                    // class/batch kernels: 8 (64 registers) or 9 (56) blocks of 128 threads per SM
+    int minb = 9;                    // class/batch kernels: 9 (56 registers) or 8 (64) blocks of 128 threads per SM
     int rows = 1;                    // batch: rows per tile
     int ctas_per_sm = 0;             // batch: resident blocks per SM of the persistent grid (0 = occupancy)
     int graph = 1;                   // batch, persistent mode: launch through a CUDA graph

@@ -66,16 +66,20 @@ def pick(a, idx):
     return None if a is None else a[idx]
 
 
-def check_parity(g, prm, noise, sh, gpu, pixels=None, min_agree=0.98):
-    """Compare GPU results (full frame arrays) with the oracle on `pixels` (all if None)."""
+def check_parity(g, prm, noise, sh, gpu, pixels=None, min_agree=0.98, gathered=False):
+    """Compare GPU results with the oracle on `pixels` (all if None).  `gpu` holds full-frame
+    arrays, or with gathered=True one row per entry of `pixels`, in that order."""
     H, W = g.depth.shape
     prob = oracle.Problem(g, prm, noise, sh)
     if pixels is None:
         xy = oracle.all_pixels(H, W)
     else:
         xy = np.ascontiguousarray(np.asarray(pixels, dtype=np.int32).reshape(-1, 2))
-    idx = xy[:, 1].astype(np.int64) * W + xy[:, 0]
-    g0, g1, gm = gpu[0][idx], pick(gpu[1], idx), gpu[2][idx]
+    if gathered:
+        g0, g1, gm = gpu
+    else:
+        idx = xy[:, 1].astype(np.int64) * W + xy[:, 0]
+        g0, g1, gm = gpu[0][idx], pick(gpu[1], idx), gpu[2][idx]
     r0, r1, rm = oracle.fp32(prob, xy)
     e0, e1, em, margin = oracle.fp64(prob, xy)
     # G1: bitmasks bit-exact against the binary32 replica

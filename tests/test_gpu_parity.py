@@ -11,7 +11,7 @@ import pytest
 import oracle
 import scenegen
 from scenegen import Params
-from tests.gpu_util import check_parity, run_gpu, sample_pixels
+from tests.gpu_util import check_parity, run_gpu, sample_pixels, to_device
 
 pytestmark = pytest.mark.gpu
 
@@ -60,6 +60,9 @@ SMALL = [
     # pair's second step idle
     (200, 150, 23, dict(num_slices=3, steps_per_side=7, radius=0.5), True),
     (201, 149, 24, dict(num_slices=2, steps_per_side=9, radius=0.4, step_mode=1, sector_count=64), True),
+    # the largest width and height the ABI accepts, each with a handful of pixels across
+    (16384, 5, 25, dict(num_slices=2, steps_per_side=6), True),
+    (6, 16384, 26, dict(num_slices=2, steps_per_side=6, sector_count=64, ambient_cones=2), True),
 ]
 
 
@@ -163,6 +166,54 @@ def test_4k_precision_form_sampled(ctx, nb):
     H, W = w.gbuf.depth.shape
     info = check_parity(w.gbuf, w.params, w.noise, w.sh, res, pixels=sample_pixels(H, W, 12000, 2))
     assert info["agree"] > 0.98
+
+
+def test_maximum_frame_sampled(ctx):
+    """The largest frame the ABI accepts, 16384 x 16384 (2^28 pixels: the largest grid, pixel
+    coordinates and mask offsets), FP16 normal/radiance, ambient cones and the masks of every
+    slice; checked on sampled pixels (corners, edge midpoints and uniform draws), gathered on the
+    device so that no full-frame array crosses to the host."""
+    import torch
+
+    import paper_2301_11376_gb300 as ssilvb
+    N = 16384
+    g = scenegen.render(31, N, N, 64, 16).as_f16()
+    prm = Params(num_slices=2, steps_per_side=8, ambient_cones=2)
+    noise, sh = scenegen.ign_table(), scenegen.sh_environment(7)
+    d, n, r = to_device(g)
+    out0, out1, m = ssilvb.alloc_outputs(N, N, prm, "cuda", masks=True)
+    out0.fill_(-7.0)
+    ctx.gather(d, n, r, g.camera, prm, out0, out1, m, noise=noise, sh=sh)
+    torch.cuda.synchronize()
+    del d, n, r
+    xy = sample_pixels(N, N, 3000, 6)
+    idx = torch.from_numpy(xy[:, 1].astype(np.int64) * N + xy[:, 0]).cuda()
+    o0 = out0.view(-1, 4)[idx].cpu().numpy().astype(np.float64)
+    o1 = out1.view(-1, 4)[idx].cpu().numpy().astype(np.float64)
+    mk = m.view(prm.num_slices, -1)[:, idx].cpu().numpy().view(np.uint32).T.astype(np.uint64)
+    del out0, out1, m
+    torch.cuda.empty_cache()
+    info = check_parity(g, prm, noise, sh, (o0, o1, mk), pixels=xy, gathered=True)
+    assert info["agree"] > 0.98
+
+
+def test_empty_and_oversized_frames_rejected(ctx):
+    """Frames with no rows or no columns, and frames wider or taller than 16384 pixels, are
+    rejected before any launch (INVALID_ARG) and leave the outputs untouched."""
+    import torch
+
+    import paper_2301_11376_gb300 as ssilvb
+    cam = scenegen.Camera(16.0, 16.0, 16.0, 16.0)
+    for H, W in [(0, 32), (32, 0), (1, 16385), (16385, 1)]:
+        d = torch.ones((H, W), device="cuda")
+        n = torch.zeros((H, W, 4), device="cuda")
+        r = torch.zeros((H, W, 4), device="cuda")
+        out0 = torch.full((H, W, 4), 5.0, device="cuda")
+        with pytest.raises(ssilvb.SsilvbError) as ei:
+            ctx.gather(d, n, r, cam, Params(), out0, None, None)
+        assert ei.value.code == 1
+        torch.cuda.synchronize()
+        assert torch.all(out0 == 5.0)
 
 
 def test_host_buffers_equal_device_buffers(ctx):
