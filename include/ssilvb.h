@@ -142,7 +142,7 @@ typedef enum {
 
 typedef struct {
     int mapping;          /* ssilvb_mapping, single-frame calls */
-    int occupancy;        /* 0 (default: 9), or 8 / 9: blocks of 128 threads per SM the register budget is sized for */
+    int occupancy;        /* 0 (default: 8 for N_b 32, else 9), or 8 / 9: blocks of 128 threads per SM the register budget is sized for */
     int rows_per_tile;    /* batch: 0, or 1..8 image rows per work item */
     int ctas_per_sm;      /* batch: 0 (as many as fit), or 1..16 blocks per SM in the persistent grid */
     int use_graph;        /* batch, persistent mode: 0 auto, 1 launch through a cached CUDA graph, 2 plain */

@@ -32,6 +32,7 @@ namespace ssilvb {
 
 constexpr int kMaxSlices = 16;
 constexpr int kMaxCones = 8;
+constexpr int kSlots = 9;  // shared-memory words per thread for slice-end state (gather_pixel)
 
 // Everything a launch needs, passed by value as a __grid_constant__ parameter.
 struct GatherParams {
@@ -370,11 +371,12 @@ __device__ __forceinline__ void march_side(const GatherParams &P, const Pixel &X
         // Steps 0 .. J-1 provably stay on screen when the offset of step J-1 does (offsets grow with
         // j), which holds when ceil(o |w| + 1) is within the pixels left to the screen edge in this
         // side's direction along each axis (|round(o w)| <= o |w| + 1/2); and if the first step is
-        // off the centre pixel so are the rest.  Each lane estimates its J from the inverse of the
-        // offset formula, then confirms it with that exact bound, stepping back at most twice.  The
-        // warp runs the smallest J (in whole step pairs) without the per-step screen and centre
-        // tests, then the remaining steps with them.  (A copy of the checked loop rather than a
-        // template parameter of one loop: the shared form compiled to 3 % slower code.)
+        // off the centre pixel so are the rest.  Each lane takes J = N_s when the last step fits,
+        // else estimates J from the inverse of the offset formula and confirms it with that exact
+        // bound, stepping back at most twice.  The warp runs the smallest J (in whole step pairs)
+        // without the per-step screen and centre tests, then the remaining steps with them.  (A
+        // copy of the checked loop rather than a template parameter of one loop: the shared form
+        // compiled to 3 % slower code.)
         float o_first;
         if (STEP_MODE == 0) {
             o_first = fmaf(1.0f, X.del, X.xdel);
@@ -387,10 +389,6 @@ __device__ __forceinline__ void march_side(const GatherParams &P, const Pixel &X
         if (off_centre) {
             const float ax = fabsf(wsx), ay = fabsf(wsy);
             const int dxi = wsx >= 0.0f ? P.W - 1 - x : x, dyi = wsy >= 0.0f ? P.H - 1 - y : y;
-            const float t = fminf(((float)dxi - 1.0f) / ax, ((float)dyi - 1.0f) / ay);
-            const float jm = STEP_MODE == 0 ? (t - X.xdel) / X.del
-                                            : (sqrtf(fmaxf(t, 0.0f) / X.rpx) - X.xidn) / X.dn_;
-            J = (int)fminf(fmaxf(floorf(jm), 0.0f), (float)P.ns);
             auto fits = [&](int n) {  // step n - 1 (and so every earlier step) on screen
                 float o;
                 if (STEP_MODE == 0) {
@@ -401,9 +399,24 @@ __device__ __forceinline__ void march_side(const GatherParams &P, const Pixel &X
                 }
                 return __float2int_ru(fmaf(o, ax, 1.0f)) <= dxi && __float2int_ru(fmaf(o, ay, 1.0f)) <= dyi;
             };
-            if (J > 0 && !fits(J)) {
-                --J;
-                if (J > 0 && !fits(J)) J = 0;
+            if (fits(P.ns)) {
+                J = P.ns;
+            } else {
+                // only an estimate (fast approximate division and square root; NaN converts to
+                // 0): fits() decides
+                const float t = fminf(__fdividef((float)dxi - 1.0f, ax), __fdividef((float)dyi - 1.0f, ay));
+                float jm;
+                if (STEP_MODE == 0) {
+                    jm = __fdividef(t - X.xdel, X.del);
+                } else {
+                    const float q = __fdividef(fmaxf(t, 0.0f), X.rpx);
+                    jm = __fdividef(q * rsqrtf(q) - X.xidn, X.dn_);
+                }
+                J = min(max(__float2int_rd(jm), 0), P.ns);
+                if (J > 0 && !fits(J)) {
+                    --J;
+                    if (J > 0 && !fits(J)) J = 0;
+                }
             }
         }
         const int Jw = __reduce_min_sync(__activemask(), J);
@@ -483,8 +496,14 @@ __device__ __forceinline__ void march_side(const GatherParams &P, const Pixel &X
 
 // The whole per-pixel gather (Algorithm 1 with Sections 3.2 and 3.3) for pixel (x, y) of
 // noise class cls = (y & 3) * 4 + (x & 3).
-template <int NB, bool F16, bool INF_T, int STEP_MODE>
-__device__ __forceinline__ void gather_pixel(const GatherParams &P, int x, int y) {
+//
+// The state a slice touches only at its end (AO and ambient sums, and the slice frame cg, sg, s the
+// ambient cones need) lives in shared memory: kSlots words per thread, word k at sl[k * STRIDE],
+// STRIDE the block's thread count.  Kept in registers it is live across both step loops, and at 9
+// blocks of 128 threads per SM the register budget then spills; in shared memory it costs a few
+// accesses per slice.  `volatile` keeps each access a real one.
+template <int NB, bool F16, bool INF_T, int STEP_MODE, int STRIDE>
+__device__ __forceinline__ void gather_pixel(const GatherParams &P, int x, int y, volatile float *sl) {
     using M = typename MaskT<NB>::T;
     const float z = __ldg(P.depth + (unsigned)y * (unsigned)P.depth_pitch + (unsigned)x);
     float4 *o0 = reinterpret_cast<float4 *>(P.out0 + (size_t)y * P.out0_pitch) + x;
@@ -527,7 +546,12 @@ __device__ __forceinline__ void gather_pixel(const GatherParams &P, int x, int y
         X.m2t = -2.0f * X.tp;
     }
 
-    float AO = 0.0f, GIr = 0.0f, GIg = 0.0f, GIb = 0.0f, AMr = 0.0f, AMg = 0.0f, AMb = 0.0f;
+    // slots: 0 AO, 1-3 ambient rgb, 4 cg, 5 sg, 6-8 s
+    sl[0] = 0.0f;
+    sl[STRIDE] = 0.0f;
+    sl[2 * STRIDE] = 0.0f;
+    sl[3 * STRIDE] = 0.0f;
+    float GIr = 0.0f, GIg = 0.0f, GIb = 0.0f;
     for (int i = 0; i < P.nd; ++i) {
         const float cphi = P.dcos[cls][i], sphi = P.dsin[cls][i];
         // Slice plane: s = normalize(w3 - (w3.v) v), w3 the view-space image of omega.
@@ -558,6 +582,11 @@ __device__ __forceinline__ void gather_pixel(const GatherParams &P, int x, int y
         const float thr_m = cu_m >= 0.0f ? su_m : (su_m > 0.0f ? 2.0f : -2.0f);
 
         M b = 0;
+        sl[4 * STRIDE] = cg;
+        sl[5 * STRIDE] = sg;
+        sl[6 * STRIDE] = sx;
+        sl[7 * STRIDE] = sy;
+        sl[8 * STRIDE] = sz;
         // Side -omega, then side +omega (Section 3.3: nearer samples occlude later ones first).
         march_side<NB, F16, INF_T, STEP_MODE, false>(P, X, x, y, cphi, sphi, off, thr_m * fabsf(thr_m), b,
                                                      GIr, GIg, GIb);
@@ -565,8 +594,11 @@ __device__ __forceinline__ void gather_pixel(const GatherParams &P, int x, int y
                                                     GIr, GIg, GIb);
 
         // Slice end: unoccluded fraction, then the ambient cones (Section 3.2).
-        AO += (float)(NB - popc_(b)) * P.inv_nb;
+        sl[0] = sl[0] + (float)(NB - popc_(b)) * P.inv_nb;
         if (P.na > 0) {
+            const float cg = sl[4 * STRIDE], sg = sl[5 * STRIDE];
+            const float sx = sl[6 * STRIDE], sy = sl[7 * STRIDE], sz = sl[8 * STRIDE];
+            float AMr = sl[STRIDE], AMg = sl[2 * STRIDE], AMb = sl[3 * STRIDE];
             const int g = NB / P.na;
             for (int k = 0; k < P.na; ++k) {
                 const M Mk = run_mask<NB>(k * g, (k + 1) * g);
@@ -599,15 +631,18 @@ __device__ __forceinline__ void gather_pixel(const GatherParams &P, int x, int y
                 AMg = fmaf(wt, L1, AMg);
                 AMb = fmaf(wt, L2, AMb);
             }
+            sl[STRIDE] = AMr;
+            sl[2 * STRIDE] = AMg;
+            sl[3 * STRIDE] = AMb;
         }
         if (P.masks) reinterpret_cast<M *>(P.masks)[((size_t)i * P.H + y) * P.W + x] = b;
     }
     const float gr = GIr * P.inv_nd, gg = GIg * P.inv_nd, gb = GIb * P.inv_nd;
-    *o0 = make_float4(gr, gg, gb, AO * P.inv_nd);
+    *o0 = make_float4(gr, gg, gb, sl[0] * P.inv_nd);
     if (P.light_out) write_light<F16>(P, x, y, gr, gg, gb);
     if (P.na > 0)
         *(reinterpret_cast<float4 *>(P.out1 + (size_t)y * P.out1_pitch) + x) =
-            make_float4(AMr * P.inv_nd, AMg * P.inv_nd, AMb * P.inv_nd, 0.0f);
+            make_float4(sl[STRIDE] * P.inv_nd, sl[2 * STRIDE] * P.inv_nd, sl[3 * STRIDE] * P.inv_nd, 0.0f);
 }
 
 // Natural mapping: one thread per pixel, 32 x 8 pixel tiles.
@@ -616,7 +651,8 @@ __global__ void __launch_bounds__(256) gather_tile_kernel(const __grid_constant_
     const int x = blockIdx.x * 32 + (threadIdx.x & 31);
     const int y = P.y0 + blockIdx.y * 8 + (threadIdx.x >> 5);
     if (x >= P.W || y >= P.y1) return;
-    gather_pixel<NB, F16, INF_T, STEP_MODE>(P, x, y);
+    __shared__ float slots[kSlots * 256];
+    gather_pixel<NB, F16, INF_T, STEP_MODE, 256>(P, x, y, slots + threadIdx.x);
 }
 
 // Class-strided mapping.  A warp takes 8 x 4 pixels at stride 4 of a 32 x 16 pixel patch, all of
@@ -638,7 +674,8 @@ __global__ void __launch_bounds__(128, MINB) gather_class_kernel(const __grid_co
     patch_pixel(blockIdx.x >> 2, blockIdx.y, blockIdx.x & 3, x, y);
     y += P.y0;
     if (x >= P.W || y >= P.y1) return;
-    gather_pixel<NB, F16, INF_T, STEP_MODE>(P, x, y);
+    __shared__ float slots[kSlots * 128];
+    gather_pixel<NB, F16, INF_T, STEP_MODE, 128>(P, x, y, slots + threadIdx.x);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -668,6 +705,7 @@ __global__ void __launch_bounds__(128, MINB)
                         unsigned *__restrict__ queue) {
     __shared__ GatherParams sP;
     __shared__ int s_tile, s_frame;
+    __shared__ float slots[kSlots * 128];
     const int n_frames = hdr->n_frames, total = hdr->total_tiles;
     int cur = -1;
     for (;;) {
@@ -696,7 +734,7 @@ __global__ void __launch_bounds__(128, MINB)
             int x, y;
             patch_pixel(xb >> 2, band * rows + r, xb & 3, x, y);
             if (y >= sP.H) break;
-            if (x < sP.W) gather_pixel<NB, F16, INF_T, STEP_MODE>(sP, x, y);
+            if (x < sP.W) gather_pixel<NB, F16, INF_T, STEP_MODE, 128>(sP, x, y, slots + threadIdx.x);
         }
         __syncthreads();  // everyone is done with s_tile, s_frame and sP before they change
     }

@@ -32,12 +32,16 @@ struct HostLane {
 // A resolved launch choice.  Every choice gives bit-identical results.
 struct KernelChoice {
     int mapping = SSILVB_MAP_CLASS;  // single frame: SSILVB_MAP_TILE or SSILVB_MAP_CLASS
-    int minb = 9;                    // class/batch kernels: 9 (56 registers) or 8 (64) blocks of 128 threads per SM
+    int minb = 9;                    // class/batch kernels: 8 (64 registers) or 9 (56) blocks of 128 threads per SM
     int rows = 1;                    // batch: rows per tile
     int ctas_per_sm = 0;             // batch: resident blocks per SM of the persistent grid (0 = occupancy)
     int graph = 1;                   // batch, persistent mode: launch through a CUDA graph
     int batch_mode = 2;              // batch: 1 persistent tile queue, 2 graph of per-frame kernels
 };
+
+// Default register budget of the class and batch kernels (measured at 4K, CUDA events): 8 blocks of
+// 128 threads per SM for N_b = 32 (1 % faster than 9), 9 for N_b = 64 and 128 (1.5 % faster than 8).
+inline int default_minb(int nb) { return nb == 32 ? 8 : 9; }
 
 cudaError_t launch_single_nb32(const GatherParams &P, bool f16, bool inf_t, const KernelChoice &k, cudaStream_t s);
 cudaError_t launch_single_nb64(const GatherParams &P, bool f16, bool inf_t, const KernelChoice &k, cudaStream_t s);

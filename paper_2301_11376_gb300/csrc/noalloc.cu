@@ -87,6 +87,7 @@ extern "C" ssilvb_status ssilvb_gather_batch_noalloc(const ssilvb_frame *frames,
     // The work list, built on this call's stack (no heap), then copied into the scratch.
     KernelChoice k;  // library defaults: class-strided warps, one row per work item
     k.rows = 1;
+    k.minb = default_minb(nb);
     alignas(16) unsigned char host[kQueueOffset];
     BatchHeader *hdr = reinterpret_cast<BatchHeader *>(host);
     FrameDesc *fd = reinterpret_cast<FrameDesc *>(host + sizeof(BatchHeader));

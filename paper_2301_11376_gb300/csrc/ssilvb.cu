@@ -247,6 +247,7 @@ TuneKey tune_key(const ssilvb_gbuffer *g, const ssilvb_params *p, int batch) {
 
 KernelChoice resolve_choice(const ssilvb_ctx *ctx, const TuneKey &key) {
     KernelChoice k;
+    k.minb = default_minb(key.nb);
     auto it = ctx->tuned.find(key);
     if (it != ctx->tuned.end()) k = it->second;
     const ssilvb_tuning &t = ctx->tuning;
