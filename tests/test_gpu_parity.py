@@ -56,10 +56,13 @@ SMALL = [
     (40, 30, 18, dict(num_slices=2, steps_per_side=1), True),                  # one step: a pair's second half idle
     (40, 30, 19, dict(num_slices=2, steps_per_side=6, radius=1e6), True),      # projected radius at its 2^20 cap
     (40, 30, 20, dict(num_slices=2, steps_per_side=6, radius=1e-4), True),     # every step on the centre pixel
-    # small radius on a larger frame: most warps take the check-free loop; odd N_s leaves its last
+    # small radius on a larger frame: the unchecked prefix loop covers whole sides; odd N_s leaves its last
     # pair's second step idle
     (200, 150, 23, dict(num_slices=3, steps_per_side=7, radius=0.5), True),
     (201, 149, 24, dict(num_slices=2, steps_per_side=9, radius=0.4, step_mode=1, sector_count=64), True),
+    # most sides leave the screen part-way: each warp's unchecked prefix, then the checked steps
+    (320, 180, 27, dict(num_slices=2, steps_per_side=24, radius=3.0), True),
+    (320, 180, 28, dict(num_slices=2, steps_per_side=23, radius=3.0, step_mode=1, sector_count=128), True),
     # the largest width and height the ABI accepts, each with a handful of pixels across
     (16384, 5, 25, dict(num_slices=2, steps_per_side=6), True),
     (6, 16384, 26, dict(num_slices=2, steps_per_side=6, sector_count=64, ambient_cones=2), True),
