@@ -57,7 +57,7 @@ def _load():
         lib = ctypes.CDLL(build())
         P = ctypes.POINTER(_Problem)
         vp = ctypes.c_void_p
-        lib.orc64_pixels.argtypes = [P, ctypes.c_int, vp, vp, vp, vp, vp]
+        lib.orc64_pixels.argtypes = [P, ctypes.c_int, vp, vp, vp, vp, vp, vp]
         lib.orc32_pixels.argtypes = [P, ctypes.c_int, vp, vp, vp, vp, vp]
         lib.orc32_set_trace.argtypes = [vp]
         lib.orc32_acos.argtypes = [ctypes.c_float]
@@ -126,18 +126,22 @@ def _pixels(prob: Problem, pixels):
     return np.ascontiguousarray(np.asarray(pixels, dtype=np.int32).reshape(-1, 2))
 
 
-def fp64(prob: Problem, pixels=None):
+def fp64(prob: Problem, pixels=None, ratio: bool = False):
     """FP64 oracle on the listed (x, y) pixels (all when None).
-    Returns out0 [n,4], out1 [n,4], masks [n,N_d] uint64 ([n,N_d,2] for N_b = 128), margin [n,N_d]."""
+    Returns out0 [n,4], out1 [n,4], masks [n,N_d] uint64 ([n,N_d,2] for N_b = 128), margin [n,N_d],
+    and with ratio=True also ratio [n,N_d]: per slice, the smallest ratio of a hit-rule decision's
+    distance from its boundary to the binary32 error bound of the endpoints it depends on."""
     xy = _pixels(prob, pixels)
     n = xy.shape[0]
     o0 = np.zeros((n, 4)); o1 = np.zeros((n, 4))
     m = np.zeros((n, prob.nd, prob.words), dtype=np.uint64); g = np.zeros((n, prob.nd))
+    r = np.zeros((n, prob.nd)) if ratio else None
     rc = _load().orc64_pixels(ctypes.byref(prob.c), n, xy.ctypes.data, o0.ctypes.data, o1.ctypes.data,
-                              m.ctypes.data, g.ctypes.data)
+                              m.ctypes.data, g.ctypes.data, r.ctypes.data if ratio else None)
     if rc != 0:
         raise ValueError(f"orc64_pixels rejected the problem (code {rc})")
-    return o0, o1, (m[..., 0] if prob.words == 1 else m), g
+    out = (o0, o1, (m[..., 0] if prob.words == 1 else m), g)
+    return out + (r,) if ratio else out
 
 
 def fp32(prob: Problem, pixels=None, counts: bool = False):

@@ -44,10 +44,12 @@ typedef struct {
 /* Per pixel listed in xy ([n*2] = x, y): out0[4] = (GI.rgb, AO), out1[4] = (ambient.rgb, 0),
  * masks[N_d][words] (words = 2 for N_b = 128, else 1; sector k is bit k % 64 of word k / 64),
  * margin[N_d] = smallest distance, in sector units, of any
- * hit-rule decision of that slice from its rounding boundary.  Any output pointer may be NULL.
- * Returns 0, or a nonzero code for an invalid problem. */
+ * hit-rule decision of that slice from its rounding boundary, and ratio[N_d] = smallest ratio of
+ * such a distance to a bound on how far the binary32 evaluation of that decision's endpoints can
+ * lie from these FP64 values (a ratio above 1: binary32 takes the same decision).  Any output
+ * pointer may be NULL.  Returns 0, or a nonzero code for an invalid problem. */
 int orc64_pixels(const orc_problem *pb, int n, const int32_t *xy, double *out0, double *out1,
-                 uint64_t *masks, double *margin);
+                 uint64_t *masks, double *margin, double *ratio);
 
 /* Same, in the binary32 arithmetic of the gather.  counts (may be NULL) receives
  * [0] pixels, [1] sky pixels, [2] slices, [3] samples visited, [4] samples skipped,

@@ -123,6 +123,38 @@ static double decision_margin(double A, double B, double rawA, double rawB, int 
     return mw < m ? mw : m;
 }
 
+/* Error bound of the binary32 evaluation, used only to tell rounding-level disagreements from real
+ * ones.  eps = 2^-24 is the unit roundoff of binary32.  An angle taken as acos(c) from a cosine c
+ * known to within dc has error at most dc / sqrt(1 - c^2), and never more than 2.23 sqrt(dc): acos
+ * is Hoelder continuous with exponent 1/2 and constant pi/sqrt(2) (attained at the ends, where
+ * acos(1 - d) ~ sqrt(2 d)).  1e-7 rad covers the own arccosine's polynomial error (2e-8) and the
+ * rounding of its evaluation. */
+static const double kEps32 = 5.9604644775390625e-8;
+
+static double acos_error(double c, double dc) {
+    const double s2 = 1.0 - c * c;
+    double e = 2.23 * sqrt(dc);
+    if (s2 > 0.0 && dc / sqrt(s2) < e) e = dc / sqrt(s2);
+    return e + 1e-7;
+}
+
+/* Same decisions as decision_margin, each distance divided by the error bound of the endpoints it
+ * depends on (eA, eB in sector units). */
+static double decision_ratio(double A, double B, double rawA, double rawB, int nb, int hit_rule, double eA,
+                             double eB) {
+    if (hit_rule == 0) {
+        double r = fabs((B - A) - 0.5) / (eA + eB);
+        const double ra = frac_dist(A - 0.5) / eA, rb = frac_dist(B + 0.5) / eB;
+        if (ra < r) r = ra;
+        if (rb < r) r = rb;
+        return r;
+    }
+    const double pa = pinned(rawA, nb), pb = pinned(rawB, nb);
+    double r = (pa >= 0.0 ? pa : frac_dist(A)) / eA;
+    const double rw = (pa >= 0.0 && pb >= 0.0 && A == B) ? (pa < pb ? pa / eA : pb / eB) : frac_dist(B - A) / (eA + eB);
+    return rw < r ? rw : r;
+}
+
 /* Real spherical harmonics, 3 bands, in the order
  * Y00, Y1-1 (y), Y10 (z), Y11 (x), Y2-2 (xy), Y2-1 (yz), Y20 (3z^2-1), Y21 (xz), Y22 (x^2-y^2). */
 static void sh9(d3 w, double Y[9]) {
@@ -157,7 +189,7 @@ static int validate(const orc_problem *pb) {
 }
 
 int orc64_pixels(const orc_problem *pb, int n, const int32_t *xy, double *out0, double *out1,
-                 uint64_t *masks, double *margin) {
+                 uint64_t *masks, double *margin, double *ratio) {
     int bad = validate(pb);
     if (bad) return bad;
     const int W = pb->width, H = pb->height, nd = pb->num_slices, ns = pb->steps_per_side;
@@ -180,6 +212,7 @@ int orc64_pixels(const orc_problem *pb, int n, const int32_t *xy, double *out0, 
                 if (masks)
                     for (int w = 0; w < words; ++w) masks[((size_t)pi * nd + i) * words + w] = 0;
                 if (margin) margin[(size_t)pi * nd + i] = INFINITY;
+                if (ratio) ratio[(size_t)pi * nd + i] = INFINITY;
             }
             continue;
         }
@@ -221,10 +254,13 @@ int orc64_pixels(const orc_problem *pb, int n, const int32_t *xy, double *out0, 
                 gamma = acos(clampd(nv / pn, -1.0, 1.0));
                 if (nsd < 0.0) gamma = -gamma;
             }
+            /* Binary32 error of gamma: n.v and n.s carry a few roundings of unit vectors, and
+             * dividing by |projN| scales them up when the projected normal is short. */
+            const double e_gamma = pn > 0.0 ? acos_error(nv / pn, 16.0 * kEps32 / pn) : M_PI;
 
             unsigned char occ[128];
             memset(occ, 0, sizeof(occ));
-            double mrg = INFINITY;
+            double mrg = INFINITY, rto = INFINITY;
 
             for (int side = 0; side < 2; ++side) {
                 const int sigma = side == 0 ? -1 : 1;
@@ -273,6 +309,31 @@ int orc64_pixels(const orc_problem *pb, int n, const int32_t *xy, double *out0, 
                     sector_set(A, B, nb, pb->hit_rule, bj);
                     const double m = decision_margin(A, B, rawA, rawB, nb, pb->hit_rule);
                     if (m < mrg) mrg = m;
+                    if (ratio) {
+                        /* Binary32 error bounds of the two endpoints, in sector units.  The
+                         * components of l = s_f - p carry a few roundings of values as large as
+                         * |p| and |s_f| (8 eps of each, generously), which the cosine l.v/|l| sees
+                         * divided by |l|: close samples cancel.  The back cosine adds the
+                         * thickness and the cancellation in |l_b|^2 = |l|^2 + t^2 - 2 t l.v. */
+                        const double El = 8.0 * kEps32 * (plen + len3(sf));
+                        const double cf = clampd(dot3(l, vhat) / llen, -1.0, 1.0);
+                        const double ef = acos_error(cf, 3.5 * El / llen + 12.0 * kEps32);
+                        double eb = 0.0;
+                        if (!inf_t) {
+                            const d3 lb = sub3(add3(sf, mul3(p, tp / plen)), p);
+                            const double lbl = len3(lb), dv = dot3(l, vhat);
+                            const double cb = clampd(dot3(lb, vhat) / lbl, -1.0, 1.0);
+                            const double dcb = 3.5 * (El + 8.0 * kEps32 * tp) / lbl + 12.0 * kEps32 +
+                                               4.0 * kEps32 * (llen * llen + tp * tp + 2.0 * tp * fabs(dv)) / (lbl * lbl);
+                            eb = acos_error(cb, dcb);
+                        }
+                        const double K = nb / M_PI, eround = 8.0 * kEps32 * nb;
+                        const double eXf = K * (ef + e_gamma) + eround;
+                        const double eXb = inf_t ? eround : K * (eb + e_gamma) + eround;
+                        const double eA = Xf < Xb ? eXf : eXb, eB = Xf < Xb ? eXb : eXf;
+                        const double r = decision_ratio(A, B, rawA, rawB, nb, pb->hit_rule, eA, eB);
+                        if (r < rto) rto = r;
+                    }
 
                     /* Indirect light: each newly occluded sector carries c_j cos cos / N_b. */
                     int newly = 0;
@@ -322,6 +383,7 @@ int orc64_pixels(const orc_problem *pb, int n, const int32_t *xy, double *out0, 
                 for (int w = 0; w < words; ++w) masks[((size_t)pi * nd + i) * words + w] = bm[w];
             }
             if (margin) margin[(size_t)pi * nd + i] = mrg;
+            if (ratio) ratio[(size_t)pi * nd + i] = rto;
         }
         if (o0) { o0[0] = GI[0] / nd; o0[1] = GI[1] / nd; o0[2] = GI[2] / nd; o0[3] = AO / nd; }
         if (o1) { o1[0] = AMB[0] / nd; o1[1] = AMB[1] / nd; o1[2] = AMB[2] / nd; o1[3] = 0.0; }

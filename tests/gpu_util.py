@@ -2,8 +2,9 @@
 it with the CPU oracle.
 
 Gates: (G1) bitmasks bit-exact against the binary32 replica; (G3) every FP64/binary32 mask
-disagreement explained by an FP64 decision within 1e-3 sector units of its rounding
-boundary; (G2) AO, GI and ambient within 1e-4 of the FP64 oracle on every pixel none of
+disagreement explained by an FP64 decision that lies within the binary32 error bound of its
+endpoints from its rounding boundary (the oracle's ratio <= 1; the bound grows where an angle is
+taken from a cosine near +-1 and where a sample lies close to the centre point); (G2) AO, GI and ambient within 1e-4 of the FP64 oracle on every pixel none of
 whose hit-rule decisions lies within 1e-4 sector units of a boundary.  On the remaining pixels the two
 precisions may credit a sector to different samples (GI credits each sector to the first
 sample that covers it) or flip it: there the difference is bounded by a few sectors' share,
@@ -14,9 +15,9 @@ import numpy as np
 import oracle
 
 TOL = 1e-4          # absolute, AO / GI / ambient vs the FP64 oracle
-MARGIN_TOL = 1e-3   # sector units: a mask flip must come from a decision this close to its boundary
 CLEAR_TOL = 1e-4    # sector units: decisions this far from every boundary agree in both precisions
-                    # (the largest binary32 endpoint error observed is ~3e-6 sector units)
+                    # (typical binary32 endpoint errors are ~3e-6 sector units; a decision that
+                    # flips anyway leaves the comparison through the mask agreement test)
 
 
 def to_device(g, pad: int = 0):
@@ -81,15 +82,15 @@ def check_parity(g, prm, noise, sh, gpu, pixels=None, min_agree=0.98, gathered=F
         idx = xy[:, 1].astype(np.int64) * W + xy[:, 0]
         g0, g1, gm = gpu[0][idx], pick(gpu[1], idx), gpu[2][idx]
     r0, r1, rm = oracle.fp32(prob, xy)
-    e0, e1, em, margin = oracle.fp64(prob, xy)
+    e0, e1, em, margin, ratio = oracle.fp64(prob, xy, ratio=True)
     # G1: bitmasks bit-exact against the binary32 replica
     bad = np.argwhere(gm != rm)
     assert bad.size == 0, f"{len(bad)} bitmasks differ from the replica, first at pixel {xy[bad[0][0]]}"
-    # G3: FP64 vs binary32 mask disagreements only at rounding boundaries
+    # G3: FP64 vs binary32 mask disagreements only within the binary32 error bound of a boundary
     diff = em != rm
     if diff.ndim == 3:
         diff = diff.any(axis=2)
-    assert np.all(margin[diff] < MARGIN_TOL), f"unexplained mask flip, margin {margin[diff].max()}"
+    assert np.all(ratio[diff] <= 1.0), f"unexplained mask flip, distance / error bound {ratio[diff].max()}"
     agree = ~diff.any(axis=1)
     assert agree.mean() >= min_agree, agree.mean()
     # G2: continuous outputs within 1e-4 of FP64 where no decision is near a boundary
