@@ -60,6 +60,8 @@ def _load():
         lib.orc64_pixels.argtypes = [P, ctypes.c_int, vp, vp, vp, vp, vp, vp]
         lib.orc32_pixels.argtypes = [P, ctypes.c_int, vp, vp, vp, vp, vp]
         lib.orc32_set_trace.argtypes = [vp]
+        lib.orc32_set_endpoint_trace.argtypes = [vp]
+        lib.orc64_set_endpoint_trace.argtypes = [vp]
         lib.orc32_acos.argtypes = [ctypes.c_float]
         lib.orc32_acos.restype = ctypes.c_float
         lib.orc32_rsqrt.argtypes = [ctypes.c_float]
@@ -224,3 +226,26 @@ def rsqrt32_sweep(lo: float, hi: float, n: int) -> float:
 
 def lib():
     return _load()
+
+
+def endpoint_trace(prob: Problem, pixels):
+    """Per (pixel, slice, side, step): the replica's unclamped binary32 sector coordinates
+    (X_f, X_b) [n, N_d, 2, N_s, 2] float32 and the FP64 oracle's (X_f, X_b, e_f, e_b)
+    [n, N_d, 2, N_s, 4] float64, e the binary32 error bound of each endpoint; NaN where a side did
+    not compute that value (sample off screen, on the centre pixel, over sky, or skipped in the
+    edge band).  Test diagnostics."""
+    xy = _pixels(prob, pixels)
+    n = xy.shape[0]
+    ns = prob.c.steps_per_side
+    e32 = np.full((n, prob.nd, 2, ns, 2), np.nan, dtype=np.float32)
+    e64 = np.full((n, prob.nd, 2, ns, 4), np.nan, dtype=np.float64)
+    lib = _load()
+    lib.orc32_set_endpoint_trace(e32.ctypes.data)
+    lib.orc64_set_endpoint_trace(e64.ctypes.data)
+    try:
+        fp32(prob, xy)
+        fp64(prob, xy)
+    finally:
+        lib.orc32_set_endpoint_trace(None)
+        lib.orc64_set_endpoint_trace(None)
+    return e32, e64

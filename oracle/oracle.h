@@ -63,6 +63,15 @@ int orc32_pixels(const orc_problem *pb, int n, const int32_t *xy, float *out0, f
  * sector and adds indirect light; the caller zeroes it.  Used by the warp-layout study in tests. */
 void orc32_set_trace(uint8_t *trace);
 
+/* Endpoint traces, test diagnostics: while set, each orc32_pixels call writes the unclamped
+ * binary32 sector coordinates (X_f, X_b) of every sample that reaches the front angle, and each
+ * orc64_pixels call writes (X_f, X_b, e_f, e_b), the unclamped FP64 coordinates and their
+ * binary32 error bounds, for every sample it visits, at entry ((pixel * N_d + slice) * 2 + side)
+ * * N_s + step of a buffer of 2 (binary32) or 4 (FP64) values per entry.  Entries of samples not
+ * reached are left as they were.  Pass NULL to stop. */
+void orc32_set_endpoint_trace(float *buf);
+void orc64_set_endpoint_trace(double *buf);
+
 /* The replica's own arccosine (Abramowitz and Stegun 4.4.46 in binary32), exposed for tests. */
 float orc32_acos(float x);
 /* The replica's own reciprocal square root (integer seed + 3 Newton steps), for tests. */

@@ -188,6 +188,9 @@ static int validate(const orc_problem *pb) {
     return 0;
 }
 
+static double *g_endpoints = NULL;
+void orc64_set_endpoint_trace(double *buf) { g_endpoints = buf; }
+
 int orc64_pixels(const orc_problem *pb, int n, const int32_t *xy, double *out0, double *out1,
                  uint64_t *masks, double *margin, double *ratio) {
     int bad = validate(pb);
@@ -309,7 +312,7 @@ int orc64_pixels(const orc_problem *pb, int n, const int32_t *xy, double *out0, 
                     sector_set(A, B, nb, pb->hit_rule, bj);
                     const double m = decision_margin(A, B, rawA, rawB, nb, pb->hit_rule);
                     if (m < mrg) mrg = m;
-                    if (ratio) {
+                    if (ratio || g_endpoints) {
                         /* Binary32 error bounds of the two endpoints, in sector units.  The
                          * components of l = s_f - p carry a few roundings of values as large as
                          * |p| and |s_f| (8 eps of each, generously), which the cosine l.v/|l| sees
@@ -333,6 +336,13 @@ int orc64_pixels(const orc_problem *pb, int n, const int32_t *xy, double *out0, 
                         const double eA = Xf < Xb ? eXf : eXb, eB = Xf < Xb ? eXb : eXf;
                         const double r = decision_ratio(A, B, rawA, rawB, nb, pb->hit_rule, eA, eB);
                         if (r < rto) rto = r;
+                        if (g_endpoints) {
+                            double *ep = g_endpoints + 4 * ((((size_t)pi * nd + i) * 2 + side) * ns + j);
+                            ep[0] = Xf_raw;
+                            ep[1] = Xb_raw;
+                            ep[2] = eXf;
+                            ep[3] = eXb;
+                        }
                     }
 
                     /* Indirect light: each newly occluded sector carries c_j cos cos / N_b. */

@@ -141,6 +141,8 @@ static int validate(const orc_problem *pb) {
 
 static uint8_t *g_trace = NULL;
 void orc32_set_trace(uint8_t *trace) { g_trace = trace; }
+static float *g_endpoints = NULL;
+void orc32_set_endpoint_trace(float *buf) { g_endpoints = buf; }
 
 int orc32_pixels(const orc_problem *pb, int n, const int32_t *xy, float *out0, float *out1,
                  uint64_t *masks, int64_t *counts) {
@@ -310,9 +312,12 @@ int orc32_pixels(const orc_problem *pb, int n, const int32_t *xy, float *out0, f
                     if (dv * fabsf(dv) < thr2 * ll) continue;
                     uint8_t *tr = g_trace ? g_trace + (((size_t)pi * nd + i) * 2 + side) * ns + j : NULL;
                     if (tr) *tr = 1;
+                    float *ep = g_endpoints ? g_endpoints + 2 * ((((size_t)pi * nd + i) * 2 + side) * ns + j) : NULL;
                     const float rl = orc32_rsqrt(ll);
                     const float cf = dv * rl;
-                    const float Xf = fminf(fmaxf(fmaf(orc32_acos(cf), sK, off), 0.0f), f_nb);
+                    const float Xf_raw = fmaf(orc32_acos(cf), sK, off);
+                    const float Xf = fminf(fmaxf(Xf_raw, 0.0f), f_nb);
+                    if (ep) ep[0] = Xf_raw;
                     ops += OPS_FRONT_ANGLE;
                     /* The same band in sector units (exact for the computed endpoint). */
                     if (pos ? Xf > edge_hi : Xf < edge_lo) continue;
@@ -325,7 +330,9 @@ int orc32_pixels(const orc_problem *pb, int n, const int32_t *xy, float *out0, f
                         const float dvb = dv - tp;
                         const float llb = fmaf(m2t, dv, ll + t2);
                         const float cb = dvb * orc32_rsqrt(llb);
-                        Xb = fminf(fmaxf(fmaf(orc32_acos(cb), sK, off), 0.0f), f_nb);
+                        const float Xb_raw = fmaf(orc32_acos(cb), sK, off);
+                        Xb = fminf(fmaxf(Xb_raw, 0.0f), f_nb);
+                        if (ep) ep[1] = Xb_raw;
                         ops += OPS_BACK;
                     }
                     /* The back endpoint lies toward this side's edge: [A, B] = [X_f, X_b] on side +,

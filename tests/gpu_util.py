@@ -1,23 +1,21 @@
 """Helpers shared by the GPU tests: run the CUDA gather through the C ABI and compare
 it with the CPU oracle.
 
-Gates: (G1) bitmasks bit-exact against the binary32 replica; (G3) every FP64/binary32 mask
-disagreement explained by an FP64 decision that lies within the binary32 error bound of its
+Gates: (G1) bitmasks bit-exact against the binary32 replica.  (G3) Every FP64/binary32 mask
+disagreement is explained by an FP64 decision that lies within the binary32 error bound of its
 endpoints from its rounding boundary (the oracle's ratio <= 1; the bound grows where an angle is
-taken from a cosine near +-1 and where a sample lies close to the centre point); (G2) AO, GI and ambient within 1e-4 of the FP64 oracle on every pixel none of
-whose hit-rule decisions lies within 1e-4 sector units of a boundary.  On the remaining pixels the two
-precisions may credit a sector to different samples (GI credits each sector to the first
-sample that covers it) or flip it: there the difference is bounded by a few sectors' share,
-and such pixels must stay rare.  (G4) The mean absolute error against FP64 over every
-compared pixel is at most 1e-4."""
+taken from a cosine near +-1 and where a sample lies close to the centre point).  (G2) AO, GI
+and ambient within 1e-4 of the FP64 oracle on every pixel whose masks agree and all of whose
+hit-rule decisions lie beyond that bound (ratio > 1): there both precisions take the same
+decisions, so the outputs differ by rounding only.  On the remaining pixels the two precisions
+may credit a sector to a different sample (GI credits each sector to the first sample that
+covers it) or flip it: there the difference is bounded by a few sectors' share.  (G4) The mean
+absolute error against FP64 over every compared pixel is at most 1e-4."""
 import numpy as np
 
 import oracle
 
 TOL = 1e-4          # absolute, AO / GI / ambient vs the FP64 oracle
-CLEAR_TOL = 1e-4    # sector units: decisions this far from every boundary agree in both precisions
-                    # (typical binary32 endpoint errors are ~3e-6 sector units; a decision that
-                    # flips anyway leaves the comparison through the mask agreement test)
 
 
 def to_device(g, pad: int = 0):
@@ -93,11 +91,12 @@ def check_parity(g, prm, noise, sh, gpu, pixels=None, min_agree=0.98, gathered=F
     assert np.all(ratio[diff] <= 1.0), f"unexplained mask flip, distance / error bound {ratio[diff].max()}"
     agree = ~diff.any(axis=1)
     assert agree.mean() >= min_agree, agree.mean()
-    # G2: continuous outputs within 1e-4 of FP64 where no decision is near a boundary
-    clear = agree & (margin.min(axis=1) >= CLEAR_TOL)
-    # the floor/ceil rule flips on samples lying in the tangent plane to rounding, so fewer of its
-    # pixels are far from every boundary; the fraction only guards against a vacuous comparison
-    assert clear.mean() >= (min_agree - 0.05 if prm.hit_rule == 0 else 0.7), clear.mean()
+    # G2: continuous outputs within 1e-4 of FP64 where every decision lies beyond its binary32
+    # error bound.  The bound is conservative (measured endpoint errors stay below a sixth of it),
+    # so fewer pixels qualify at N_b = 128 and for the floor/ceil rule, which flips on samples lying
+    # in the tangent plane to rounding; the floor only guards against a vacuous comparison.
+    clear = agree & (ratio.min(axis=1) > 1.0)
+    assert clear.mean() >= (0.75 if prm.hit_rule == 0 else 0.6), clear.mean()
     err0 = np.abs(g0[clear] - e0[clear]).max(initial=0.0)
     assert err0 <= TOL, err0
     if prm.ambient_cones > 0:

@@ -438,3 +438,26 @@ def test_binary32_flips_lie_within_the_error_bound(seed, kw):
         assert margin[diff].max() > 1e-3  # a flat 1e-3 sector tolerance would reject these
     # not vacuous: most slices have every decision well outside its bound
     assert np.mean(ratio <= 1.0) < 0.15
+
+
+@pytest.mark.parametrize("seed,W,H,kw", [
+    (28, 320, 180, dict(num_slices=2, steps_per_side=23, radius=3.0, step_mode=1, sector_count=128)),
+    (17, 200, 150, dict(num_slices=3, steps_per_side=12, radius=2.0, thickness=0.1, thickness_slope=0.05)),
+    (1, 256, 256, dict(num_slices=4, steps_per_side=8, sector_count=64, hit_rule=1)),
+])
+def test_binary32_endpoints_within_the_error_bound(seed, W, H, kw):
+    """Every sector coordinate the replica computes (front and back, before clamping) lies within
+    the FP64 oracle's binary32 error bound of the FP64 value, over every sample of a frame, and the
+    bound stays well below a sector for the median sample."""
+    g = scenegen.render(seed, W, H, 8, 3)
+    prm = Params(**kw)
+    e32, e64 = oracle.endpoint_trace(oracle.Problem(g, prm, scenegen.ign_table()), None)
+    n = 0
+    for k in range(2):
+        x32 = e32[..., k].astype(np.float64)
+        x64, bound = e64[..., k], e64[..., 2 + k]
+        ok = np.isfinite(x32) & np.isfinite(x64)
+        n += ok.sum()
+        assert np.all(np.abs(x32[ok] - x64[ok]) <= bound[ok]), np.max(np.abs(x32[ok] - x64[ok]) / bound[ok])
+        assert np.median(bound[ok]) < 0.05 * prm.sector_count / 32
+    assert n > 100000
