@@ -257,6 +257,68 @@ def test_single_sample_gi_closed_form(step_mode, step):
     np.testing.assert_allclose(r0[0, :3], gi, atol=2e-6)
 
 
+def test_a_sector_both_sides_cover_is_credited_to_the_minus_side():
+    """Under the floor/ceil rule both sides of a slice can set the sector that straddles the split
+    between them.  Side -omega runs first, then side +omega (near to far within each side,
+    Section 3.3 credits a sector to the first sample that sets it), so that sector's indirect
+    light comes from the -omega sample.  One sample on each side, just off the view ray and far in
+    front of p, with different radiance; gamma puts the split in the middle of sector N_b/2 - 1.
+    The -omega sample is credited ceil(X_f-) sectors, the +omega one N_b - floor(X_f+) - 1;
+    crediting +omega first, or both, gives a different GI."""
+    W = H = 31
+    fx = 15.5
+    cam = scenegen.Camera(fx, fx, 15.5, 15.5)
+    c, d = 15, 2
+    nb = 32
+    z, zq = float(np.float32(7.45)), 1.0  # the depths as stored (binary32)
+    gam = math.pi / (2 * nb)
+    n_p = np.array([math.sin(gam), 0.0, math.cos(gam)], dtype=np.float32)
+    radius = float(np.float32(2 * d * z / fx))
+    offs = G.sample_offsets(radius, fx, z, 1)
+    assert int(np.rint(offs[0])) == d
+    depth = np.full((H, W), np.inf, dtype=np.float32)
+    depth[c, c] = z
+    nrm = np.zeros((H, W, 4), dtype=np.float32)
+    nrm[c, c, :3] = n_p
+    rad = np.zeros((H, W, 4), dtype=np.float32)
+    cols = {-1: np.array([0.9, 0.2, 0.1], dtype=np.float32), 1: np.array([0.1, 0.3, 0.8], dtype=np.float32)}
+    nq = np.array([0.0, 0.0, -1.0], dtype=np.float32)
+    for sigma in (-1, 1):
+        depth[c, c + sigma * d] = zq
+        nrm[c, c + sigma * d, :3] = nq
+        rad[c, c + sigma * d, :3] = cols[sigma]
+    g = scenegen.GBuffer(depth, nrm, rad, cam)
+    prm = Params(num_slices=1, steps_per_side=1, radius=radius, thickness=INF, sector_count=nb, hit_rule=1)
+
+    # closed form: t = infinity puts each back endpoint on its side's hemisphere edge
+    p, v, s, gamma = G.frame(cam, c, c, z, n_p.astype(np.float64), np.float32(1.0), np.float32(0.0))
+    assert abs(gamma - gam) < 1e-7
+    X, w = {}, {}
+    for sigma in (-1, 1):
+        l = G.unproject(cam, c + sigma * d + 0.5, c + 0.5, zq) - p
+        lh = l / np.linalg.norm(l)
+        X[sigma] = G.sector_coord(sigma * math.acos(float(np.dot(lh, v))), gamma, nb)
+        w[sigma] = (max(0.0, float(np.dot(n_p, lh))) * max(0.0, float(-np.dot(nq, lh))) / nb
+                    * cols[sigma].astype(np.float64))
+    assert nb / 2 - 1 < X[-1] < nb / 2 - 0.5 < X[1] < nb / 2  # both cover sector N_b/2 - 1
+    minus = set(range(0, math.ceil(X[-1])))
+    plus = set(range(math.floor(X[1]), nb))
+    assert nb // 2 - 1 in minus & plus
+    new_plus = plus - minus
+    gi = len(minus) * w[-1] + len(new_plus) * w[1]
+    mask = sum(1 << k for k in minus | plus)
+    swapped = (len(minus) - 1) * w[-1] + len(plus) * w[1]
+    assert np.abs(gi - swapped).max() > 1e-3
+
+    o0, _, masks, _ = oracle.fp64(oracle.Problem(g, prm, None), pixels=[(c, c)])
+    assert int(masks[0, 0]) == mask
+    np.testing.assert_allclose(o0[0, :3], gi, rtol=1e-12, atol=1e-15)
+    assert o0[0, 3] == 1.0 - len(minus | plus) / nb
+    r0, _, rmask = oracle.fp32(oracle.Problem(g, prm, None), pixels=[(c, c)])
+    assert int(rmask[0, 0]) == mask
+    np.testing.assert_allclose(r0[0, :3], gi, atol=2e-6)
+
+
 def test_two_overlapping_samples_credit_the_nearer_first():
     """Section 3.3: samples are taken near to far and a sector's indirect light comes from the
     first sample that occludes it.  Two samples on the +omega side of slice 0 (steps 0 and 1)
