@@ -249,17 +249,17 @@ int orc64_pixels(const orc_problem *pb, int n, const int32_t *xy, double *out0, 
             d3 s = sub3(w3, mul3(vhat, dot3(w3, vhat)));
             s = mul3(s, 1.0 / len3(s));
 
-            /* Projected normal angle gamma = sign(n.s) acos(n.v / |projN|), 0 if projN = 0. */
+            /* Projected normal angle gamma: the signed angle from v to the normal's projection
+             * into the slice plane, atan2(n.s, n.v); 0 if the projection is 0. */
             const double nv = dot3(np_, vhat), nsd = dot3(np_, s);
             const double pn = sqrt(nv * nv + nsd * nsd);
-            double gamma = 0.0;
-            if (pn > 0.0) {
-                gamma = acos(clampd(nv / pn, -1.0, 1.0));
-                if (nsd < 0.0) gamma = -gamma;
-            }
-            /* Binary32 error of gamma: n.v and n.s carry a few roundings of unit vectors, and
-             * dividing by |projN| scales them up when the projected normal is short. */
-            const double e_gamma = pn > 0.0 ? acos_error(nv / pn, 16.0 * kEps32 / pn) : M_PI;
+            const double gamma = pn > 0.0 ? atan2(nsd, nv) : 0.0;
+            /* Binary32 error of gamma: n.v and n.s carry a few roundings of unit vectors (16 eps,
+             * generously), scaled up by 1/|projN| when the projected normal is short.  The
+             * binary32 spec takes |gamma| as an arccosine of whichever of cos and sin is below
+             * 1/sqrt(2) in magnitude, where acos has slope at most sqrt(2); 3e-7 rad covers the own
+             * arccosine, pi/2 in binary32 and the final rounding. */
+            const double e_gamma = pn > 0.0 ? 1.5 * 16.0 * kEps32 / pn + 3e-7 : M_PI;
 
             unsigned char occ[128];
             memset(occ, 0, sizeof(occ));

@@ -35,6 +35,9 @@
 /* Algorithmic op counts per block: one per IEEE add/sub/mul/fma/div/sqrt, compare, select,
  * min/max, conversion, shift, logic op and popcount the code below performs (memory loads and
  * stores are not ops).  W = 64-bit words of the mask (2 for 128 sectors, else 1). */
+/* pi/2 rounded to binary32 */
+static const float kHalfPi32 = 1.57079637050628662109375f;
+
 #define RSQRT_OPS 13          /* max, shift, subtract, half, 3 x (square, fma, multiply) */
 #define ACOS_OPS 13           /* 1 - a, max, sqrt, 7 fma, multiply, compare, select */
 #define OPS_STEP_HEAD 12      /* loop compare + increment, j+1 and its conversion, offset fma,
@@ -241,7 +244,7 @@ int orc32_pixels(const orc_problem *pb, int n, const int32_t *xy, float *out0, f
             const float sx0 = fmaf(-wv, vx, w3x), sy0 = fmaf(-wv, vy, w3y), sz0 = -(wv * vz);
             const float rs = orc32_rsqrt(fmaf(sx0, sx0, fmaf(sy0, sy0, sz0 * sz0)));
             const float sx = sx0 * rs, sy = sy0 * rs, sz = sz0 * rs;
-            /* Projected normal: gamma = sign(n.s) acos(n.v / |projN|). */
+            /* Projected normal: gamma, the signed angle from v to n projected into the slice plane. */
             const float nv = fmaf(nx, vx, fmaf(ny, vy, nz * vz));
             const float nsd = fmaf(nx, sx, fmaf(ny, sy, nz * sz));
             const float pn2 = fmaf(nv, nv, nsd * nsd);
@@ -250,9 +253,17 @@ int orc32_pixels(const orc_problem *pb, int n, const int32_t *xy, float *out0, f
                 const float rpn = orc32_rsqrt(pn2);
                 cg = nv * rpn;
                 sg = nsd * rpn;
-                gam = orc32_acos(cg);
+                /* |gamma| from whichever of its cosine and sine is the smaller in magnitude, where
+                 * the arccosine is well conditioned: within pi/4 of 0 or pi, |gamma| = asin|sg|
+                 * = pi/2 - acos|sg| (cg >= 0) or pi/2 + acos|sg| (cg < 0); else acos(cg). */
+                if (fabsf(sg) <= fabsf(cg)) {
+                    const float a = orc32_acos(fabsf(sg));
+                    gam = cg >= 0.0f ? kHalfPi32 - a : kHalfPi32 + a;
+                } else {
+                    gam = orc32_acos(cg);
+                }
                 if (nsd < 0.0f) gam = -gam;
-                ops += RSQRT_OPS + 2 + ACOS_OPS + 2;
+                ops += RSQRT_OPS + 2 + ACOS_OPS + 2 + 4;
             }
             const float off = fmaf(-gam, K, half_nb);
             /* Cosine thresholds of the edge bands: a front direction whose cosine to v is below

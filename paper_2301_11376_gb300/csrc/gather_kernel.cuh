@@ -157,6 +157,7 @@ __device__ __forceinline__ float2 own_acos_pair(float2 c) {
 
 // 1.5 * 2^23: adding it to |v| < 2^22 leaves round(v) in the low mantissa bits.
 constexpr float kMagic = 12582912.0f;
+constexpr float kHalfPi = 1.57079637050628662109375f;  // pi/2 rounded to binary32
 constexpr int kMagicBits = 0x4B400000;
 
 // Bits [lo, min(lo + cnt, 32)) of a 32-bit word, lo, cnt >= 0 (0 when lo >= 32 or cnt == 0).
@@ -569,7 +570,15 @@ __device__ __forceinline__ void gather_pixel(const GatherParams &P, int x, int y
             const float rpn = own_rsqrt(pn2);
             cg = nv * rpn;
             sg = nsd * rpn;
-            gam = own_acos(cg);
+            // |gamma| from whichever of its cosine and sine is the smaller in magnitude, where the
+            // arccosine is well conditioned: within pi/4 of 0 or pi, |gamma| = asin|sg| =
+            // pi/2 - acos|sg| (cg >= 0) or pi/2 + acos|sg| (cg < 0); else acos(cg).
+            if (fabsf(sg) <= fabsf(cg)) {
+                const float a = own_acos(fabsf(sg));
+                gam = cg >= 0.0f ? kHalfPi - a : kHalfPi + a;
+            } else {
+                gam = own_acos(cg);
+            }
             if (nsd < 0.0f) gam = -gam;
         }
         const float off = fmaf(-gam, P.K, P.half_nb);
