@@ -516,14 +516,21 @@ def test_binary32_flips_lie_within_the_error_bound(seed, kw):
     (28, 320, 180, dict(num_slices=2, steps_per_side=23, radius=3.0, step_mode=1, sector_count=128)),
     (17, 200, 150, dict(num_slices=3, steps_per_side=12, radius=2.0, thickness=0.1, thickness_slope=0.05)),
     (1, 256, 256, dict(num_slices=4, steps_per_side=8, sector_count=64, hit_rule=1)),
+    (3, 3840, 2160, None),  # the 4K workload (FP16 normal/radiance, 4 cones) on 1500 sampled pixels
 ])
 def test_binary32_endpoints_within_the_error_bound(seed, W, H, kw):
     """Every sector coordinate the replica computes (front and back, before clamping) lies within
     the FP64 oracle's binary32 error bound of the FP64 value, over every sample of a frame, and the
     bound stays well below a sector for the median sample."""
-    g = scenegen.render(seed, W, H, 8, 3)
-    prm = Params(**kw)
-    e32, e64 = oracle.endpoint_trace(oracle.Problem(g, prm, scenegen.ign_table()), None)
+    if kw is None:
+        w = scenegen.workload_4k()
+        g, prm, noise, sh = w.gbuf, w.params, w.noise, w.sh
+        rng = np.random.default_rng(4)
+        pixels = np.stack([rng.integers(0, W, 1500), rng.integers(0, H, 1500)], 1).astype(np.int32)
+    else:
+        g = scenegen.render(seed, W, H, 8, 3)
+        prm, noise, sh, pixels = Params(**kw), scenegen.ign_table(), None, None
+    e32, e64 = oracle.endpoint_trace(oracle.Problem(g, prm, noise, sh), pixels)
     n = 0
     for k in range(2):
         x32 = e32[..., k].astype(np.float64)
