@@ -460,6 +460,49 @@ def test_linear_environment_ambient_closed_form():
     np.testing.assert_allclose(o1[0, :3], expect, rtol=1e-12, atol=1e-14)
 
 
+@pytest.mark.parametrize("func", ["z2", "x2-y2"])
+def test_quadratic_environment_ambient_is_the_cone_average(func):
+    """Band-2 SH coefficients that represent a known quadratic function f of the world direction:
+    the ambient term must be the average of f over the cone directions.  f = z^2 = 1/3 + (2/3)
+    P2(z) (Legendre), i.e. c00 = 2 sqrt(pi)/3 and c20 = (4/3) sqrt(pi/5); f = x^2 - y^2, the
+    projection 4 sqrt(pi/15) onto Y22.  Unoccluded pixel on the optical axis facing the camera,
+    view-to-world rotated 20 degrees about x: gamma = 0, cone k of slice i points along
+    cos(th_k) v + sin(th_k) s_i, th_k = -pi/2 + (k + 1/2) pi / N_a (Section 3.2), each cone
+    weighted 1/N_a."""
+    W = H = 33
+    g = scenegen.hand_quad_over_sky(W, H, depth=3.0, x0=0, x1=W, y0=0, y1=H)
+    th = math.radians(20.0)
+    R = np.array([[1, 0, 0], [0, math.cos(th), -math.sin(th)], [0, math.sin(th), math.cos(th)]], dtype=np.float32)
+    g.camera.view_to_world = R
+    sh = np.zeros((9, 3), dtype=np.float32)
+    if func == "z2":
+        sh[0] = 2.0 * math.sqrt(math.pi) / 3.0
+        sh[6] = 4.0 / 3.0 * math.sqrt(math.pi / 5.0)
+        f = lambda w: w[2] * w[2]  # noqa: E731
+    else:
+        sh[8] = 4.0 * math.sqrt(math.pi / 15.0)
+        f = lambda w: w[0] * w[0] - w[1] * w[1]  # noqa: E731
+    nd, na = 4, 4
+    prm = Params(num_slices=nd, steps_per_side=5, radius=1.0, ambient_cones=na)
+    c = W // 2
+    o0, o1, masks, _ = oracle.fp64(oracle.Problem(g, prm, None, sh), pixels=[(c, c)])
+    assert np.all(masks == 0)
+    Rd = R.astype(np.float64)
+    v = np.array([0.0, 0.0, 1.0])
+    expect = 0.0
+    for i in range(nd):
+        cphi, sphi = G.slice_dir(i, nd)
+        _, _, s_i, gamma = G.frame(g.camera, c, c, 3.0, v, cphi, sphi)
+        assert abs(gamma) < 1e-12
+        for k in range(na):
+            t = -math.pi / 2 + (k + 0.5) * math.pi / na
+            expect += f(Rd @ (math.cos(t) * v + math.sin(t) * s_i)) / (nd * na)
+    # the sample's FP32 rounding of the coefficients is the only difference from f itself
+    np.testing.assert_allclose(o1[0, :3], expect, rtol=2e-7, atol=1e-12)
+    r0, r1, _ = oracle.fp32(oracle.Problem(g, prm, None, sh), pixels=[(c, c)])
+    np.testing.assert_allclose(r1[0, :3], expect, atol=2e-6)
+
+
 # --- the binary32 replica against the FP64 oracle on a seeded frame ---------------------------
 
 def test_replica_vs_fp64_on_256():
