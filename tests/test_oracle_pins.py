@@ -201,15 +201,17 @@ def test_step_wall_closed_form(thickness, axis):
 
 # --- single sample: closed-form indirect light (Algorithm 1 GI line, Section 3.3) -------------
 
-@pytest.mark.parametrize("step_mode,step,nb,slope", [(0, 0, 32, 0.0), (1, 2, 32, 0.0), (0, 1, 128, 0.05),
-                                                    (1, 3, 64, 0.05)])
-def test_single_sample_gi_closed_form(step_mode, step, nb, slope):
+@pytest.mark.parametrize("step_mode,step,nb,slope,nd", [(0, 0, 32, 0.0, 1), (1, 2, 32, 0.0, 1), (0, 1, 128, 0.05, 1),
+                                                       (1, 3, 64, 0.05, 1), (0, 0, 32, 0.0, 2)])
+def test_single_sample_gi_closed_form(step_mode, step, nb, slope, nd):
     """Sky everywhere except the centre pixel p and one pixel q on step `step` of the +omega
     side of slice 0 (constant steps, or quadratic steps r ((j+1)/(N_s+1))^2: the reading taken of
     the growing step lengths of Section 4.3).
     The result is that sample alone: cnt sectors of its slab,
     GI = cnt/N_b * c_q * max(0, n_p.l) * max(0, -n_q.l) / N_d.  Also for 64 and 128 sectors
-    (sector k is bit k % 64 of word k / 64) and a thickness t0 + slope z_p growing with depth."""
+    (sector k is bit k % 64 of word k / 64), a thickness t0 + slope z_p growing with depth, and
+    N_d = 2, whose second (vertical) slice sees only sky: GI and occlusion are averaged over the
+    slices."""
     W = H = 31
     fx = 15.5
     cam = scenegen.Camera(fx, fx, 15.5, 15.5)
@@ -231,7 +233,7 @@ def test_single_sample_gi_closed_form(step_mode, step, nb, slope):
     cq = np.array([0.9, 0.4, 0.2], dtype=np.float32)
     rad[c, c + dq, :3] = cq
     g = scenegen.GBuffer(depth, nrm, rad, cam)
-    prm = Params(num_slices=1, steps_per_side=ns, radius=radius, thickness=t0, thickness_slope=slope,
+    prm = Params(num_slices=nd, steps_per_side=ns, radius=radius, thickness=t0, thickness_slope=slope,
                  sector_count=nb, step_mode=step_mode)
 
     # closed form
@@ -249,8 +251,8 @@ def test_single_sample_gi_closed_form(step_mode, step, nb, slope):
     assert cnt >= 2
     lh = l / np.linalg.norm(l)
     w = cnt / nb * max(0.0, float(np.dot(n_p, lh))) * max(0.0, float(-np.dot(nq.astype(np.float64), lh)))
-    gi = w * cq.astype(np.float64)
-    ao = 1.0 - cnt / nb
+    gi = w * cq.astype(np.float64) / nd
+    ao = (1.0 - cnt / nb + (nd - 1)) / nd  # the other slice (vertical) sees only sky
 
     def as_int(words):
         words = np.atleast_1d(words)
@@ -258,6 +260,7 @@ def test_single_sample_gi_closed_form(step_mode, step, nb, slope):
 
     o0, _, masks, _, ratio = oracle.fp64(oracle.Problem(g, prm, None), pixels=[(c, c)], ratio=True)
     assert as_int(masks[0, 0]) == m
+    assert all(as_int(masks[0, i]) == 0 for i in range(1, nd))
     np.testing.assert_allclose(o0[0, :3], gi, rtol=1e-12, atol=1e-15)
     assert abs(o0[0, 3] - ao) < 1e-15
     # the replica must take the same decisions: each lies beyond its binary32 error bound
