@@ -166,9 +166,9 @@ def test_infinite_thickness_equals_quantised_horizon(nb):
 
 # --- single infinite wall: closed-form occluded fraction (Section 3.1) ------------------------
 
-@pytest.mark.parametrize("axis", [0, 1])
+@pytest.mark.parametrize("axis,xi", [(0, None), (1, None), (0, (0.37, 0.5)), (1, (0.37, 0.25))])
 @pytest.mark.parametrize("thickness", [INF, 2.0])
-def test_step_wall_closed_form(thickness, axis):
+def test_step_wall_closed_form(thickness, axis, xi):
     """Centre pixel on the back plane at the principal point (gamma = 0).  A wall face at
     x = X_w (axis 0), or a ledge edge at y = -X_w below the centre (axis 1), rises H_w toward
     the camera.  Slice phi steps along (cos phi, sin phi) in pixels with image y down, i.e.
@@ -176,21 +176,32 @@ def test_step_wall_closed_form(thickness, axis):
     its top edge is at in-plane distance X_w/|c|, and the occluded sectors are the
     N_b (pi/2 - h*)/pi nearest the hemisphere edge of the side facing it (sectors N_b-1 down
     for side +omega, 0 up for side -omega), h* = atan2(X_w/|c|, H_w).  Holds for t = inf and
-    any t >= H_w."""
+    any t >= H_w, as long as the samples reach the top edge.  With a noise table, slice i lies at
+    (i + xi_phi) pi / N_d and the steps are jittered by xi_s (Algorithm 1, directions and steps
+    with random offsets): no slice is then parallel to the step, and every one must see it at its
+    rotated angle."""
     W = H = 255
     z0, xw, hw, nb = 4.0, 0.6, 1.5, 32
     g = scenegen.hand_step_wall(W, H, z0, xw, hw, axis=axis)
-    prm = Params(num_slices=4, steps_per_side=48, radius=3.0, thickness=thickness, sector_count=nb)
+    radius = 3.0 if xi is None else 4.0  # oblique slices need the longer reach
+    prm = Params(num_slices=4, steps_per_side=48, radius=radius, thickness=thickness, sector_count=nb)
     c = (W - 1) // 2
-    _, _, masks, _ = oracle.fp64(oracle.Problem(g, prm, None), pixels=[(c, c)])
+    noise = None
+    if xi is not None:
+        noise = np.zeros((16, 2), dtype=np.float32)
+        noise[(c & 3) * 4 + (c & 3)] = xi  # the centre pixel's class
+    _, _, masks, _ = oracle.fp64(oracle.Problem(g, prm, noise), pixels=[(c, c)])
     half = (1 << (nb // 2)) - 1
     for i in range(4):
-        phi = i * math.pi / 4
+        phi = (i + (0.0 if xi is None else float(np.float32(xi[0])))) * math.pi / 4
         toward = math.cos(phi) if axis == 0 else math.sin(phi)  # +x, or -y in view space
         m = int(masks[0, i])
         if abs(toward) < 1e-9:
             assert m == 0, (i, hex(m))
             continue
+        # the last step reaches past the top edge: its pixel offset toward the step exceeds the
+        # edge's, xw / (z0 - hw) * f / |c| pixels along the slice
+        assert radius * g.camera.fx / z0 * 48 / 49 > xw / (z0 - hw) * g.camera.fx / abs(toward)
         expect = nb * (math.pi / 2 - math.atan2(xw / abs(toward), hw)) / math.pi
         assert abs(bin(m).count("1") - expect) <= 1.0, (i, bin(m).count("1"), expect)
         if toward > 0:   # side +omega faces the step: a run ending at sector N_b - 1
