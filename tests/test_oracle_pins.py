@@ -517,6 +517,49 @@ def test_quadratic_environment_ambient_is_the_cone_average(func):
     np.testing.assert_allclose(r1[0, :3], expect, atol=2e-6)
 
 
+def test_ambient_cones_follow_the_projected_normal():
+    """With a tilted centre normal, each slice's cones are centred on its own projected normal:
+    cone k of slice i points at gamma_i - pi/2 + (k + 1/2) pi / N_a from v (Section 3.2, Eq. 4
+    frame), gamma_i = atan2(n.s_i, n.v).  A lone pixel over sky (no occlusion) with the SH
+    coefficients of f = z + z^2 (z projects onto Y10 with sqrt(4 pi / 3); z^2 as above): the
+    ambient term is f averaged over those directions in world space.  The linear part is what
+    sees gamma: the cones are evenly spaced over a half circle, so the mean of any quadratic in
+    (cos, sin) over them does not depend on gamma, while their mean direction is proportional to
+    cos(gamma) v + sin(gamma) s.  A wrong sign or a missing gamma offset fails this."""
+    W = H = 33
+    c = W // 2
+    g = scenegen.hand_quad_over_sky(W, H, depth=3.0, x0=c, x1=c + 1, y0=c, y1=c + 1)
+    n = np.array([0.45, -0.30, 0.0], dtype=np.float64)
+    n[2] = math.sqrt(1.0 - n[0] ** 2 - n[1] ** 2)
+    g.normal[c, c, :3] = n.astype(np.float32)
+    th = math.radians(20.0)
+    R = np.array([[1, 0, 0], [0, math.cos(th), -math.sin(th)], [0, math.sin(th), math.cos(th)]], dtype=np.float32)
+    g.camera.view_to_world = R
+    sh = np.zeros((9, 3), dtype=np.float32)
+    sh[0] = 2.0 * math.sqrt(math.pi) / 3.0
+    sh[2] = math.sqrt(4.0 * math.pi / 3.0)
+    sh[6] = 4.0 / 3.0 * math.sqrt(math.pi / 5.0)
+    nd, na = 4, 8
+    prm = Params(num_slices=nd, steps_per_side=5, radius=1.0, ambient_cones=na, sector_count=64)
+    o0, o1, masks, _ = oracle.fp64(oracle.Problem(g, prm, None, sh), pixels=[(c, c)])
+    assert np.all(masks == 0)
+    Rd = R.astype(np.float64)
+    nf = g.normal[c, c, :3].astype(np.float64)
+    expect, gammas = 0.0, []
+    for i in range(nd):
+        cphi, sphi = G.slice_dir(i, nd)
+        _, v, s_i, gamma = G.frame(g.camera, c, c, 3.0, nf, cphi, sphi)
+        gammas.append(gamma)
+        for k in range(na):
+            t = gamma - math.pi / 2 + (k + 0.5) * math.pi / na
+            w = Rd @ (math.cos(t) * v + math.sin(t) * s_i)
+            expect += (w[2] + w[2] * w[2]) / (nd * na)
+    assert min(abs(x) for x in gammas) > 0.05  # every slice's frame is rotated
+    np.testing.assert_allclose(o1[0, :3], expect, rtol=2e-7, atol=1e-12)
+    r0, r1, _ = oracle.fp32(oracle.Problem(g, prm, None, sh), pixels=[(c, c)])
+    np.testing.assert_allclose(r1[0, :3], expect, atol=2e-6)
+
+
 # --- the binary32 replica against the FP64 oracle on a seeded frame ---------------------------
 
 def test_replica_vs_fp64_on_256():
