@@ -5,8 +5,11 @@ CPU-baseline leg of ``bench.py`` import this package.  The product path never
 imports it and shares no code with it.
 
 ``fp64`` runs the double-precision oracle (per-sector brute force);
-``fp32`` runs the binary32 replica whose masks the GPU must equal bit for bit.
-Both are plain single-threaded C, built here with gcc and loaded by ctypes.
+``fp32`` runs the binary32 replica whose masks the GPU must equal bit for bit;
+``fp64(..., forced=True)`` evaluates the outputs in FP64 on the replica's per-sample
+sector runs (the decision-forced evaluation).  Both programs are plain C, built here
+with gcc (OpenMP over pixels where the compiler has it; results do not depend on the
+thread count) and loaded by ctypes.
 """
 from __future__ import annotations
 
@@ -28,12 +31,15 @@ CFLAGS = ["-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-ffp-contract=off", "-fno-fas
 
 
 def build(force: bool = False) -> str:
+    """Compile the oracle library, with OpenMP when gcc has it (else single-threaded)."""
     os.makedirs(_BUILD, exist_ok=True)
     srcs = [os.path.join(_HERE, s) for s in _SRCS] + [os.path.join(_HERE, "oracle.h")]
     if not force and os.path.exists(_SO) and all(os.path.getmtime(_SO) >= os.path.getmtime(s) for s in srcs):
         return _SO
     tmp = _SO + f".tmp{os.getpid()}"
-    subprocess.run(["gcc", *CFLAGS, *srcs[:-1], "-o", tmp, "-lm"], check=True, capture_output=True)
+    r = subprocess.run(["gcc", *CFLAGS, "-fopenmp", *srcs[:-1], "-o", tmp, "-lm"], capture_output=True)
+    if r.returncode != 0:
+        subprocess.run(["gcc", *CFLAGS, *srcs[:-1], "-o", tmp, "-lm"], check=True, capture_output=True)
     os.replace(tmp, _SO)
     return _SO
 
@@ -58,10 +64,11 @@ def _load():
         P = ctypes.POINTER(_Problem)
         vp = ctypes.c_void_p
         lib.orc64_pixels.argtypes = [P, ctypes.c_int, vp, vp, vp, vp, vp, vp]
+        lib.orc64_pixels_ex.argtypes = [P, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp, vp]
         lib.orc32_pixels.argtypes = [P, ctypes.c_int, vp, vp, vp, vp, vp]
-        lib.orc32_set_trace.argtypes = [vp]
-        lib.orc32_set_endpoint_trace.argtypes = [vp]
-        lib.orc64_set_endpoint_trace.argtypes = [vp]
+        lib.orc32_pixels_ex.argtypes = [P, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp]
+        lib.orc_threads.argtypes = [ctypes.c_int]
+        lib.orc_threads.restype = ctypes.c_int
         lib.orc32_acos.argtypes = [ctypes.c_float]
         lib.orc32_acos.restype = ctypes.c_float
         lib.orc32_rsqrt.argtypes = [ctypes.c_float]
@@ -128,20 +135,47 @@ def _pixels(prob: Problem, pixels):
     return np.ascontiguousarray(np.asarray(pixels, dtype=np.int32).reshape(-1, 2))
 
 
-def fp64(prob: Problem, pixels=None, ratio: bool = False):
+def threads(n: int = 0) -> int:
+    """Threads of the oracle's pixel loops: n > 0 sets the count; returns the count in use."""
+    return _load().orc_threads(int(n))
+
+
+def _chunk(prob: Problem, per_sample_bytes: int) -> int:
+    """Pixels per call so that the per-sample arrays of one call stay near 64 MB."""
+    per_pixel = prob.nd * 2 * prob.c.steps_per_side * per_sample_bytes
+    return max(1, (64 << 20) // per_pixel)
+
+
+def fp64(prob: Problem, pixels=None, ratio: bool = False, forced: bool = False):
     """FP64 oracle on the listed (x, y) pixels (all when None).
     Returns out0 [n,4], out1 [n,4], masks [n,N_d] uint64 ([n,N_d,2] for N_b = 128), margin [n,N_d],
     and with ratio=True also ratio [n,N_d]: per slice, the smallest ratio of a hit-rule decision's
-    distance from its boundary to the binary32 error bound of the endpoints it depends on."""
+    distance from its boundary to the binary32 error bound of the endpoints it depends on.
+    forced=True: the decision-forced evaluation.  Every sample sets the sector run the binary32
+    replica decides for it (run here, pixel block by pixel block) and everything else is evaluated
+    in FP64 as in the free-running oracle; its masks therefore equal the replica's."""
     xy = _pixels(prob, pixels)
     n = xy.shape[0]
     o0 = np.zeros((n, 4)); o1 = np.zeros((n, 4))
     m = np.zeros((n, prob.nd, prob.words), dtype=np.uint64); g = np.zeros((n, prob.nd))
     r = np.zeros((n, prob.nd)) if ratio else None
-    rc = _load().orc64_pixels(ctypes.byref(prob.c), n, xy.ctypes.data, o0.ctypes.data, o1.ctypes.data,
-                              m.ctypes.data, g.ctypes.data, r.ctypes.data if ratio else None)
-    if rc != 0:
-        raise ValueError(f"orc64_pixels rejected the problem (code {rc})")
+    lib = _load()
+    step = _chunk(prob, 4) if forced else max(n, 1)
+    for a in range(0, n, step):
+        b = min(n, a + step)
+        sub = np.ascontiguousarray(xy[a:b])
+        runs = None
+        if forced:
+            runs = np.zeros((b - a, prob.nd, 2, prob.c.steps_per_side, 2), dtype=np.int16)
+            rc = lib.orc32_pixels_ex(ctypes.byref(prob.c), b - a, sub.ctypes.data, None, None, None, None,
+                                     runs.ctypes.data, None)
+            if rc != 0:
+                raise ValueError(f"orc32_pixels_ex rejected the problem (code {rc})")
+        rc = lib.orc64_pixels_ex(ctypes.byref(prob.c), b - a, sub.ctypes.data, o0[a:b].ctypes.data,
+                                 o1[a:b].ctypes.data, m[a:b].ctypes.data, g[a:b].ctypes.data,
+                                 r[a:b].ctypes.data if ratio else None, runs.ctypes.data if forced else None, None)
+        if rc != 0:
+            raise ValueError(f"orc64_pixels_ex rejected the problem (code {rc})")
     out = (o0, o1, (m[..., 0] if prob.words == 1 else m), g)
     return out + (r,) if ratio else out
 
@@ -163,28 +197,17 @@ def fp32(prob: Problem, pixels=None, counts: bool = False):
     return o0, o1, m
 
 
-def sample_trace(prob: Problem, pixels) -> np.ndarray:
-    """Per-sample decisions of the binary32 replica on the listed pixels: uint8 [n, N_d, 2 sides, N_s],
-    side -omega first; bit 0: the sample passes the edge-band cosine test (full sample path),
-    bit 1: it also newly occludes a sector (indirect light)."""
+def runs32(prob: Problem, pixels=None) -> np.ndarray:
+    """The replica's sector run (lo, hi) of every sample: int16 [n, N_d, 2 sides, N_s, 2], side -omega
+    first; (0, 0) where a sample sets no sector."""
     xy = _pixels(prob, pixels)
     n = xy.shape[0]
-    ns = prob.c.steps_per_side
-    tr = np.zeros((n, prob.nd, 2, ns), dtype=np.uint8)
-    lib = _load()
-    lib.orc32_set_trace(tr.ctypes.data)
-    try:
-        rc = lib.orc32_pixels(ctypes.byref(prob.c), n, xy.ctypes.data, None, None, None, None)
-    finally:
-        lib.orc32_set_trace(None)
+    runs = np.zeros((n, prob.nd, 2, prob.c.steps_per_side, 2), dtype=np.int16)
+    rc = _load().orc32_pixels_ex(ctypes.byref(prob.c), n, xy.ctypes.data, None, None, None, None,
+                                 runs.ctypes.data, None)
     if rc != 0:
-        raise ValueError(f"orc32_pixels rejected the problem (code {rc})")
-    return tr
-
-
-def full_path_trace(prob: Problem, pixels) -> np.ndarray:
-    """Which samples take the full sample path in the binary32 replica: bool [n, N_d, 2, N_s]."""
-    return (sample_trace(prob, pixels) & 1).astype(bool)
+        raise ValueError(f"orc32_pixels_ex rejected the problem (code {rc})")
+    return runs
 
 
 def acos32(x: float) -> float:
@@ -240,12 +263,10 @@ def endpoint_trace(prob: Problem, pixels):
     e32 = np.full((n, prob.nd, 2, ns, 2), np.nan, dtype=np.float32)
     e64 = np.full((n, prob.nd, 2, ns, 4), np.nan, dtype=np.float64)
     lib = _load()
-    lib.orc32_set_endpoint_trace(e32.ctypes.data)
-    lib.orc64_set_endpoint_trace(e64.ctypes.data)
-    try:
-        fp32(prob, xy)
-        fp64(prob, xy)
-    finally:
-        lib.orc32_set_endpoint_trace(None)
-        lib.orc64_set_endpoint_trace(None)
+    rc = lib.orc32_pixels_ex(ctypes.byref(prob.c), n, xy.ctypes.data, None, None, None, None, None, e32.ctypes.data)
+    if rc == 0:
+        rc = lib.orc64_pixels_ex(ctypes.byref(prob.c), n, xy.ctypes.data, None, None, None, None, None, None,
+                                 e64.ctypes.data)
+    if rc != 0:
+        raise ValueError(f"oracle rejected the problem (code {rc})")
     return e32, e64

@@ -47,9 +47,23 @@ typedef struct {
  * hit-rule decision of that slice from its rounding boundary, and ratio[N_d] = smallest ratio of
  * such a distance to a bound on how far the binary32 evaluation of that decision's endpoints can
  * lie from these FP64 values (a ratio above 1: binary32 takes the same decision).  Any output
- * pointer may be NULL.  Returns 0, or a nonzero code for an invalid problem. */
+ * pointer may be NULL.  Returns 0, or a nonzero code for an invalid problem.  The pixel loop runs
+ * on orc_threads() threads; every result is independent of the thread count. */
 int orc64_pixels(const orc_problem *pb, int n, const int32_t *xy, double *out0, double *out1,
                  uint64_t *masks, double *margin, double *ratio);
+
+/* orc64_pixels with two optional per-sample arrays, laid out per listed pixel as [N_d][2 sides][N_s]
+ * entries (side -omega first):
+ *   forced (input, int16 pairs (lo, hi)): the decision-forced evaluation.  Each visited sample sets
+ *     exactly the sectors [lo, hi) (none when hi <= lo) instead of those of the FP64 hit rule; the
+ *     geometry, the cosines, the per-sector crediting of indirect light, AO and the ambient cones
+ *     stay in FP64.  Given the replica's runs (orc32_pixels_ex), it evaluates the outputs in FP64
+ *     on the binary32 decisions.  margin and ratio still describe the FP64 decisions.  Returns 11
+ *     for a run outside [0, N_b].
+ *   endpoints (output, 4 doubles): (X_f, X_b, e_f, e_b), the unclamped FP64 sector coordinates and
+ *     their binary32 error bounds, written for every visited sample, left as they were elsewhere. */
+int orc64_pixels_ex(const orc_problem *pb, int n, const int32_t *xy, double *out0, double *out1,
+                    uint64_t *masks, double *margin, double *ratio, const int16_t *forced, double *endpoints);
 
 /* Same, in the binary32 arithmetic of the gather.  counts (may be NULL) receives
  * [0] pixels, [1] sky pixels, [2] slices, [3] samples visited, [4] samples skipped,
@@ -57,20 +71,18 @@ int orc64_pixels(const orc_problem *pb, int n, const int32_t *xy, double *out0, 
 int orc32_pixels(const orc_problem *pb, int n, const int32_t *xy, float *out0, float *out1,
                  uint64_t *masks, int64_t *counts);
 
-/* Optional per-sample trace of the next orc32_pixels calls (NULL turns it off): one byte per
- * (pixel, slice, side, step), laid out [n][N_d][2][N_s]: bit 0 where the sample passes the
- * edge-band cosine test and so takes the full sample path, bit 1 where it also newly occludes a
- * sector and adds indirect light; the caller zeroes it.  Used by the warp-layout study in tests. */
-void orc32_set_trace(uint8_t *trace);
+/* orc32_pixels with two optional per-sample arrays in the layout of orc64_pixels_ex:
+ *   runs (output, int16 pairs): the sector run [lo, hi) each sample sets, (0, 0) where it sets none
+ *     (skipped, in the edge band, or an empty run); written for every entry.
+ *   endpoints (output, 2 floats): the unclamped binary32 sector coordinates (X_f, X_b) of every
+ *     sample that reaches the front angle (X_b only past the edge-band test), left as they were
+ *     elsewhere. */
+int orc32_pixels_ex(const orc_problem *pb, int n, const int32_t *xy, float *out0, float *out1,
+                    uint64_t *masks, int64_t *counts, int16_t *runs, float *endpoints);
 
-/* Endpoint traces, test diagnostics: while set, each orc32_pixels call writes the unclamped
- * binary32 sector coordinates (X_f, X_b) of every sample that reaches the front angle, and each
- * orc64_pixels call writes (X_f, X_b, e_f, e_b), the unclamped FP64 coordinates and their
- * binary32 error bounds, for every sample it visits, at entry ((pixel * N_d + slice) * 2 + side)
- * * N_s + step of a buffer of 2 (binary32) or 4 (FP64) values per entry.  Entries of samples not
- * reached are left as they were.  Pass NULL to stop. */
-void orc32_set_endpoint_trace(float *buf);
-void orc64_set_endpoint_trace(double *buf);
+/* Threads of the pixel loops: n > 0 sets the count; returns the count in use (1 when built without
+ * OpenMP). */
+int orc_threads(int n);
 
 /* The replica's own arccosine (Abramowitz and Stegun 4.4.46 in binary32), exposed for tests. */
 float orc32_acos(float x);

@@ -99,8 +99,10 @@ static int popc128(mask_t v) {
     return __builtin_popcountll((uint64_t)v) + __builtin_popcountll((uint64_t)(v >> 64));
 }
 
-static mask_t sector_run(float A, float B, int nb, int hit_rule) {
+/* The run [lo, hi) of one sample (lo >= hi: no sector), and its mask. */
+static mask_t sector_run(float A, float B, int nb, int hit_rule, int *lo_out, int *hi_out) {
     int lo, hi;
+    *lo_out = *hi_out = 0;
     if (hit_rule == 0) {
         /* sectors whose centre k + 1/2 lies in [A, B], provided B - A >= 1/2:
          * exactly the sectors covered at least half (Section 3.1 round criterion) */
@@ -113,15 +115,19 @@ static mask_t sector_run(float A, float B, int nb, int hit_rule) {
         if (hi > nb) hi = nb;
     }
     if (hi <= lo) return 0;
+    *lo_out = lo;
+    *hi_out = hi;
     return low_bits(hi) & ~low_bits(lo);
 }
 
 uint64_t orc32_sector_mask(float A, float B, int nb, int hit_rule) {
-    return (uint64_t)sector_run(A, B, nb, hit_rule);
+    int lo, hi;
+    return (uint64_t)sector_run(A, B, nb, hit_rule, &lo, &hi);
 }
 
 void orc32_sector_mask_words(float A, float B, int nb, int hit_rule, uint64_t *out2) {
-    const mask_t m = sector_run(A, B, nb, hit_rule);
+    int lo, hi;
+    const mask_t m = sector_run(A, B, nb, hit_rule, &lo, &hi);
     out2[0] = (uint64_t)m;
     out2[1] = (uint64_t)(m >> 64);
 }
@@ -142,285 +148,329 @@ static int validate(const orc_problem *pb) {
     return 0;
 }
 
-static uint8_t *g_trace = NULL;
-void orc32_set_trace(uint8_t *trace) { g_trace = trace; }
-static float *g_endpoints = NULL;
-void orc32_set_endpoint_trace(float *buf) { g_endpoints = buf; }
-
-int orc32_pixels(const orc_problem *pb, int n, const int32_t *xy, float *out0, float *out1,
-                 uint64_t *masks, int64_t *counts) {
-    int bad = validate(pb);
-    if (bad) return bad;
-    const int W = pb->width, H = pb->height, nd = pb->num_slices, ns = pb->steps_per_side;
-    const int nb = pb->sector_count, na = pb->ambient_cones;
-    const int words = nb == 128 ? 2 : 1;
-    const int inf_t = isinf(pb->thickness);
-    const int ops_run = OPS_RUN(words), ops_cone = OPS_CONE(words);
-    int64_t c_pix = 0, c_sky = 0, c_slice = 0, c_visit = 0, c_skip = 0, c_gi = 0, ops = 0;
-
-    /* Per-launch constants, binary32 unless noted. */
-    const float inv_fx = 1.0f / pb->fx, inv_fy = 1.0f / pb->fy;
-    const float kx0 = -(pb->cx * inv_fx), ninv_fy = -inv_fy, ky0 = pb->cy * inv_fy;
-    const float Rfx = pb->radius * pb->fx;
-    const float dn = 1.0f / (float)(ns + 1);
-    const float K = (float)((double)nb / M_PI); /* sectors per radian, FP64 rounded once */
-    const float half_nb = 0.5f * (float)nb, f_nb = (float)nb;
-    const float inv_nb = 1.0f / (float)nb, inv_nd = 1.0f / (float)nd;
-    const float t0 = pb->thickness, kt = pb->thickness_slope;
-    const float edge_hi = pb->hit_rule == 0 ? f_nb - 0.5f : nextafterf(f_nb, 0.0f);
-    const float edge_lo = pb->hit_rule == 0 ? 0.5f : nextafterf(0.0f, 1.0f);
-    /* half a sector in radians (0 for the floor/ceil rule), its sine and cosine, FP64 rounded once */
-    const double del = pb->hit_rule == 0 ? M_PI / (2.0 * nb) : 0.0;
-    const float sdel = (float)sin(del), cdel = (float)cos(del);
-
-    /* Direction table: cos, sin of (i + xi_phi) pi / N_d per noise class, FP64 rounded once. */
+/* Per-call constants of the replica (binary32 unless noted), shared read-only by every pixel. */
+typedef struct {
+    int W, H, nd, ns, nb, na, words, inf_t, ops_run, ops_cone;
+    float inv_fx, inv_fy, kx0, ninv_fy, ky0, Rfx, dn, K, half_nb, f_nb, inv_nb, inv_nd, t0, kt;
+    float edge_hi, edge_lo, sdel, cdel;
     float dcos[16][16], dsin[16][16];
-    for (int c = 0; c < 16; ++c) {
-        const float xi = pb->noise ? pb->noise[2 * c] : 0.0f;
-        for (int i = 0; i < nd; ++i) {
-            const double phi = ((double)i + (double)xi) * M_PI / (double)nd;
-            dcos[c][i] = (float)cos(phi);
-            dsin[c][i] = (float)sin(phi);
+    float ccos[8], csin[8];
+    float Y0, Y1, Y2, Y3, Y4;
+} ctx32;
+
+static void setup32(const orc_problem *pb, ctx32 *c) {
+    c->W = pb->width;
+    c->H = pb->height;
+    c->nd = pb->num_slices;
+    c->ns = pb->steps_per_side;
+    c->nb = pb->sector_count;
+    c->na = pb->ambient_cones;
+    c->words = c->nb == 128 ? 2 : 1;
+    c->inf_t = isinf(pb->thickness);
+    c->ops_run = OPS_RUN(c->words);
+    c->ops_cone = OPS_CONE(c->words);
+    c->inv_fx = 1.0f / pb->fx;
+    c->inv_fy = 1.0f / pb->fy;
+    c->kx0 = -(pb->cx * c->inv_fx);
+    c->ninv_fy = -c->inv_fy;
+    c->ky0 = pb->cy * c->inv_fy;
+    c->Rfx = pb->radius * pb->fx;
+    c->dn = 1.0f / (float)(c->ns + 1);
+    c->K = (float)((double)c->nb / M_PI); /* sectors per radian, FP64 rounded once */
+    c->half_nb = 0.5f * (float)c->nb;
+    c->f_nb = (float)c->nb;
+    c->inv_nb = 1.0f / (float)c->nb;
+    c->inv_nd = 1.0f / (float)c->nd;
+    c->t0 = pb->thickness;
+    c->kt = pb->thickness_slope;
+    c->edge_hi = pb->hit_rule == 0 ? c->f_nb - 0.5f : nextafterf(c->f_nb, 0.0f);
+    c->edge_lo = pb->hit_rule == 0 ? 0.5f : nextafterf(0.0f, 1.0f);
+    /* half a sector in radians (0 for the floor/ceil rule), its sine and cosine, FP64 rounded once */
+    const double del = pb->hit_rule == 0 ? M_PI / (2.0 * c->nb) : 0.0;
+    c->sdel = (float)sin(del);
+    c->cdel = (float)cos(del);
+    /* Direction table: cos, sin of (i + xi_phi) pi / N_d per noise class, FP64 rounded once. */
+    for (int k = 0; k < 16; ++k) {
+        const float xi = pb->noise ? pb->noise[2 * k] : 0.0f;
+        for (int i = 0; i < c->nd; ++i) {
+            const double phi = ((double)i + (double)xi) * M_PI / (double)c->nd;
+            c->dcos[k][i] = (float)cos(phi);
+            c->dsin[k][i] = (float)sin(phi);
         }
     }
     /* Cone table: group-centre angles -pi/2 + (k + 1/2) pi / N_a relative to the normal. */
-    float ccos[8], csin[8];
-    for (int k = 0; k < na; ++k) {
-        const double th = -0.5 * M_PI + (k + 0.5) * M_PI / na;
-        ccos[k] = (float)cos(th);
-        csin[k] = (float)sin(th);
+    for (int k = 0; k < c->na; ++k) {
+        const double th = -0.5 * M_PI + (k + 0.5) * M_PI / c->na;
+        c->ccos[k] = (float)cos(th);
+        c->csin[k] = (float)sin(th);
     }
-    const float Y0 = (float)(0.5 * sqrt(1.0 / M_PI)), Y1 = (float)sqrt(3.0 / (4.0 * M_PI));
-    const float Y2 = (float)(0.5 * sqrt(15.0 / M_PI)), Y3 = (float)(0.25 * sqrt(5.0 / M_PI));
-    const float Y4 = (float)(0.25 * sqrt(15.0 / M_PI));
+    c->Y0 = (float)(0.5 * sqrt(1.0 / M_PI));
+    c->Y1 = (float)sqrt(3.0 / (4.0 * M_PI));
+    c->Y2 = (float)(0.5 * sqrt(15.0 / M_PI));
+    c->Y3 = (float)(0.25 * sqrt(5.0 / M_PI));
+    c->Y4 = (float)(0.25 * sqrt(15.0 / M_PI));
+}
 
-    for (int pi = 0; pi < n; ++pi) {
-        const int x = xy[2 * pi], y = xy[2 * pi + 1];
-        if (x < 0 || y < 0 || x >= W || y >= H) return 10;
-        float *o0 = out0 ? out0 + 4 * pi : NULL, *o1 = out1 ? out1 + 4 * pi : NULL;
-        const size_t pix = (size_t)y * W + x;
-        const float z = pb->depth[pix];
-        ++c_pix;
-        ops += 3;
-        if (!is_geometry(z)) {
-            ++c_sky;
-            ops += 8;
-            if (o0) { o0[0] = o0[1] = o0[2] = 0.0f; o0[3] = 1.0f; }
-            if (o1) { o1[0] = o1[1] = o1[2] = o1[3] = 0.0f; }
-            if (masks)
-                for (int i = 0; i < nd * words; ++i) masks[(size_t)pi * nd * words + i] = 0;
-            continue;
+/* One pixel of the replica.  cnt[7] accumulates the counters of orc32_pixels.  runs (may be NULL):
+ * this pixel's [N_d][2][N_s] block of (lo, hi) sector runs, written for every step (0, 0 where the
+ * step sets no sector).  ep (may be NULL): this pixel's [N_d][2][N_s] block of (X_f, X_b) pairs,
+ * written only for the samples that reach the front angle (and the back one). */
+static void pixel32(const orc_problem *pb, const ctx32 *c, int x, int y, float *o0, float *o1, uint64_t *mk,
+                    int64_t *cnt, int16_t *runs, float *ep) {
+    const int W = c->W, H = c->H, nd = c->nd, ns = c->ns, nb = c->nb, na = c->na, words = c->words;
+    const size_t pix = (size_t)y * W + x;
+    const float z = pb->depth[pix];
+    int64_t ops = 3;
+    ++cnt[0];
+    if (runs) memset(runs, 0, sizeof(int16_t) * 2 * 2 * (size_t)nd * ns);
+    if (!is_geometry(z)) {
+        ++cnt[1];
+        cnt[6] += ops + 8;
+        if (o0) { o0[0] = o0[1] = o0[2] = 0.0f; o0[3] = 1.0f; }
+        if (o1) { o1[0] = o1[1] = o1[2] = o1[3] = 0.0f; }
+        if (mk)
+            for (int i = 0; i < nd * words; ++i) mk[i] = 0;
+        return;
+    }
+
+    /* Pixel setup: p, v, n_p, projected radius, step unit, thickness. */
+    const float u = (float)x + 0.5f, v = (float)y + 0.5f;
+    const float ax = fmaf(u, c->inv_fx, c->kx0), by = fmaf(v, c->ninv_fy, c->ky0);
+    const float px = ax * z, py = by * z;
+    const float rd = orc32_rsqrt(fmaf(ax, ax, fmaf(by, by, 1.0f)));
+    const float vx = -(ax * rd), vy = -(by * rd), vz = rd;
+    const float *nrm = pb->normal + 4 * pix;
+    const float nx = nrm[0], ny = nrm[1], nz = nrm[2];
+    const float rpx = fminf(c->Rfx / z, 1048576.0f);
+    const int cls = (y & 3) * 4 + (x & 3);
+    const float xi_s = pb->noise ? pb->noise[2 * cls + 1] : 0.0f;
+    const float xidn = xi_s * c->dn;
+    const float del = rpx * c->dn, xdel = xidn * rpx; /* step unit r/(N_s+1) and its jitter */
+    float tp = 0.0f, t2 = 0.0f, m2t = 0.0f;
+    if (!c->inf_t) {
+        tp = fmaf(c->kt, z, c->t0);
+        t2 = tp * tp;
+        m2t = -2.0f * tp;
+    }
+    ops += 4 + 2 + 2 + RSQRT_OPS + 2 + 2 + 1 + 3 + 4;
+
+    float AO = 0.0f, GIr = 0.0f, GIg = 0.0f, GIb = 0.0f, AMr = 0.0f, AMg = 0.0f, AMb = 0.0f;
+    for (int i = 0; i < nd; ++i) {
+        ++cnt[2];
+        const float cphi = c->dcos[cls][i], sphi = c->dsin[cls][i];
+        /* Slice plane: s = normalize(w3 - (w3.v) v), w3 = view-space image of omega. */
+        const float w3x = cphi * c->inv_fx, w3y = -(sphi * c->inv_fy);
+        const float wv = fmaf(w3x, vx, w3y * vy);
+        const float sx0 = fmaf(-wv, vx, w3x), sy0 = fmaf(-wv, vy, w3y), sz0 = -(wv * vz);
+        const float rs = orc32_rsqrt(fmaf(sx0, sx0, fmaf(sy0, sy0, sz0 * sz0)));
+        const float sx = sx0 * rs, sy = sy0 * rs, sz = sz0 * rs;
+        /* Projected normal: gamma, the signed angle from v to n projected into the slice plane. */
+        const float nv = fmaf(nx, vx, fmaf(ny, vy, nz * vz));
+        const float nsd = fmaf(nx, sx, fmaf(ny, sy, nz * sz));
+        const float pn2 = fmaf(nv, nv, nsd * nsd);
+        float cg = 1.0f, sg = 0.0f, gam = 0.0f;
+        if (pn2 > 0.0f) {
+            const float rpn = orc32_rsqrt(pn2);
+            cg = nv * rpn;
+            sg = nsd * rpn;
+            /* |gamma| from whichever of its cosine and sine is the smaller in magnitude, where
+             * the arccosine is well conditioned: within pi/4 of 0 or pi, |gamma| = asin|sg|
+             * = pi/2 - acos|sg| (cg >= 0) or pi/2 + acos|sg| (cg < 0); else acos(cg). */
+            if (fabsf(sg) <= fabsf(cg)) {
+                const float a = orc32_acos(fabsf(sg));
+                gam = cg >= 0.0f ? kHalfPi32 - a : kHalfPi32 + a;
+            } else {
+                gam = orc32_acos(cg);
+            }
+            if (nsd < 0.0f) gam = -gam;
+            ops += RSQRT_OPS + 2 + ACOS_OPS + 2 + 4;
         }
+        const float off = fmaf(-gam, c->K, c->half_nb);
+        /* Cosine thresholds of the edge bands: a front direction whose cosine to v is below
+         * thr_p (side +omega) or thr_m (side -omega) lies within the band next to that side's
+         * hemisphere edge, i.e. at an angle from v above gamma + pi/2 - delta (side +) or
+         * pi/2 - gamma - delta (side -), delta = half a sector (0 for the floor/ceil rule).
+         * Angles outside [0, pi] give 2 (every direction) or -2 (none). */
+        const float cu_p = fmaf(cg, c->cdel, sg * c->sdel), su_p = fmaf(sg, c->cdel, -(cg * c->sdel));
+        const float cu_m = fmaf(cg, c->cdel, -(sg * c->sdel)), su_m = fmaf(sg, c->cdel, cg * c->sdel);
+        const float thr_p = cu_p >= 0.0f ? -su_p : (su_p < 0.0f ? 2.0f : -2.0f);
+        const float thr_m = cu_m >= 0.0f ? su_m : (su_m > 0.0f ? 2.0f : -2.0f);
+        /* signed squares: the test "cosine below thr" is dv |dv| < thr |thr| |l|^2 */
+        const float thr2_p = thr_p * fabsf(thr_p), thr2_m = thr_m * fabsf(thr_m);
+        ops += 2 + 2 + 3 + 3 + RSQRT_OPS + 3 + 6 + 2 + 1 + 1 + 2 + 8 + 8 + 2;
 
-        /* Pixel setup: p, v, n_p, projected radius, step unit, thickness. */
-        const float u = (float)x + 0.5f, v = (float)y + 0.5f;
-        const float ax = fmaf(u, inv_fx, kx0), by = fmaf(v, ninv_fy, ky0);
-        const float px = ax * z, py = by * z, pz = -z;
-        const float rd = orc32_rsqrt(fmaf(ax, ax, fmaf(by, by, 1.0f)));
-        const float vx = -(ax * rd), vy = -(by * rd), vz = rd;
-        const float *nrm = pb->normal + 4 * pix;
-        const float nx = nrm[0], ny = nrm[1], nz = nrm[2];
-        const float rpx = fminf(Rfx / z, 1048576.0f);
-        const int cls = (y & 3) * 4 + (x & 3);
-        const float xi_s = pb->noise ? pb->noise[2 * cls + 1] : 0.0f;
-        const float xidn = xi_s * dn;
-        const float del = rpx * dn, xdel = xidn * rpx; /* step unit r/(N_s+1) and its jitter */
-        float tp = 0.0f, t2 = 0.0f, m2t = 0.0f;
-        if (!inf_t) {
-            tp = fmaf(kt, z, t0);
-            t2 = tp * tp;
-            m2t = -2.0f * tp;
-        }
-        ops += 4 + 2 + 2 + RSQRT_OPS + 2 + 2 + 1 + 3 + 4;
-        (void)pz;
-
-        float AO = 0.0f, GIr = 0.0f, GIg = 0.0f, GIb = 0.0f, AMr = 0.0f, AMg = 0.0f, AMb = 0.0f;
-        for (int i = 0; i < nd; ++i) {
-            ++c_slice;
-            const float cphi = dcos[cls][i], sphi = dsin[cls][i];
-            /* Slice plane: s = normalize(w3 - (w3.v) v), w3 = view-space image of omega. */
-            const float w3x = cphi * inv_fx, w3y = -(sphi * inv_fy);
-            const float wv = fmaf(w3x, vx, w3y * vy);
-            const float sx0 = fmaf(-wv, vx, w3x), sy0 = fmaf(-wv, vy, w3y), sz0 = -(wv * vz);
-            const float rs = orc32_rsqrt(fmaf(sx0, sx0, fmaf(sy0, sy0, sz0 * sz0)));
-            const float sx = sx0 * rs, sy = sy0 * rs, sz = sz0 * rs;
-            /* Projected normal: gamma, the signed angle from v to n projected into the slice plane. */
-            const float nv = fmaf(nx, vx, fmaf(ny, vy, nz * vz));
-            const float nsd = fmaf(nx, sx, fmaf(ny, sy, nz * sz));
-            const float pn2 = fmaf(nv, nv, nsd * nsd);
-            float cg = 1.0f, sg = 0.0f, gam = 0.0f;
-            if (pn2 > 0.0f) {
-                const float rpn = orc32_rsqrt(pn2);
-                cg = nv * rpn;
-                sg = nsd * rpn;
-                /* |gamma| from whichever of its cosine and sine is the smaller in magnitude, where
-                 * the arccosine is well conditioned: within pi/4 of 0 or pi, |gamma| = asin|sg|
-                 * = pi/2 - acos|sg| (cg >= 0) or pi/2 + acos|sg| (cg < 0); else acos(cg). */
-                if (fabsf(sg) <= fabsf(cg)) {
-                    const float a = orc32_acos(fabsf(sg));
-                    gam = cg >= 0.0f ? kHalfPi32 - a : kHalfPi32 + a;
+        mask_t b = 0;
+        for (int side = 0; side < 2; ++side) {
+            const int pos = side == 1; /* side -omega first, then +omega */
+            const float wsx = pos ? cphi : -cphi, wsy = pos ? sphi : -sphi;
+            const float sK = pos ? c->K : -c->K;
+            const float edge = pos ? c->f_nb : 0.0f;
+            const float thr2 = pos ? thr2_p : thr2_m;
+            for (int j = 0; j < ns; ++j) {
+                ++cnt[3];
+                const size_t entry = ((size_t)i * 2 + side) * ns + j;
+                /* Step offset along the direction and the nearest pixel (ties to even). */
+                float o;
+                if (pb->step_mode == 0) {
+                    o = fmaf((float)(j + 1), del, xdel);
                 } else {
-                    gam = orc32_acos(cg);
+                    const float uj = fmaf((float)(j + 1), c->dn, xidn);
+                    o = (uj * uj) * rpx;
                 }
-                if (nsd < 0.0f) gam = -gam;
-                ops += RSQRT_OPS + 2 + ACOS_OPS + 2 + 4;
-            }
-            const float off = fmaf(-gam, K, half_nb);
-            /* Cosine thresholds of the edge bands: a front direction whose cosine to v is below
-             * thr_p (side +omega) or thr_m (side -omega) lies within the band next to that side's
-             * hemisphere edge, i.e. at an angle from v above gamma + pi/2 - delta (side +) or
-             * pi/2 - gamma - delta (side -), delta = half a sector (0 for the floor/ceil rule).
-             * Angles outside [0, pi] give 2 (every direction) or -2 (none). */
-            const float cu_p = fmaf(cg, cdel, sg * sdel), su_p = fmaf(sg, cdel, -(cg * sdel));
-            const float cu_m = fmaf(cg, cdel, -(sg * sdel)), su_m = fmaf(sg, cdel, cg * sdel);
-            const float thr_p = cu_p >= 0.0f ? -su_p : (su_p < 0.0f ? 2.0f : -2.0f);
-            const float thr_m = cu_m >= 0.0f ? su_m : (su_m > 0.0f ? 2.0f : -2.0f);
-            /* signed squares: the test "cosine below thr" is dv |dv| < thr |thr| |l|^2 */
-            const float thr2_p = thr_p * fabsf(thr_p), thr2_m = thr_m * fabsf(thr_m);
-            ops += 2 + 2 + 3 + 3 + RSQRT_OPS + 3 + 6 + 2 + 1 + 1 + 2 + 8 + 8 + 2;
+                /* nearest integer (ties to even) of the exact product, via a fused add of 1.5*2^23 */
+                const float dxf = fmaf(o, wsx, 12582912.0f) - 12582912.0f;
+                const float dyf = fmaf(o, wsy, 12582912.0f) - 12582912.0f;
+                ops += OPS_STEP_HEAD + OPS_STEP_QUAD * (pb->step_mode != 0);
+                if (dxf == 0.0f && dyf == 0.0f) { ++cnt[4]; continue; }
+                const int qx = x + (int)dxf, qy = y + (int)dyf;
+                ops += OPS_STEP_PIXEL;
+                if (qx < 0 || qy < 0 || qx >= W || qy >= H) { ++cnt[4]; continue; }
+                const size_t q = (size_t)qy * W + qx;
+                const float zq = pb->depth[q];
+                ops += OPS_STEP_DEPTH;
+                if (!is_geometry(zq)) { ++cnt[4]; continue; }
 
-            mask_t b = 0;
-            for (int side = 0; side < 2; ++side) {
-                const int pos = side == 1; /* side -omega first, then +omega */
-                const float wsx = pos ? cphi : -cphi, wsy = pos ? sphi : -sphi;
-                const float sK = pos ? K : -K;
-                const float edge = pos ? f_nb : 0.0f;
-                const float thr2 = pos ? thr2_p : thr2_m;
-                for (int j = 0; j < ns; ++j) {
-                    ++c_visit;
-                    /* Step offset along the direction and the nearest pixel (ties to even). */
-                    float o;
-                    if (pb->step_mode == 0) {
-                        o = fmaf((float)(j + 1), del, xdel);
-                    } else {
-                        const float uj = fmaf((float)(j + 1), dn, xidn);
-                        o = (uj * uj) * rpx;
-                    }
-                    /* nearest integer (ties to even) of the exact product, via a fused add of 1.5*2^23 */
-                    const float dxf = fmaf(o, wsx, 12582912.0f) - 12582912.0f;
-                    const float dyf = fmaf(o, wsy, 12582912.0f) - 12582912.0f;
-                    ops += OPS_STEP_HEAD + OPS_STEP_QUAD * (pb->step_mode != 0);
-                    if (dxf == 0.0f && dyf == 0.0f) { ++c_skip; continue; }
-                    const int qx = x + (int)dxf, qy = y + (int)dyf;
-                    ops += OPS_STEP_PIXEL;
-                    if (qx < 0 || qy < 0 || qx >= W || qy >= H) { ++c_skip; continue; }
-                    const size_t q = (size_t)qy * W + qx;
-                    const float zq = pb->depth[q];
-                    ops += OPS_STEP_DEPTH;
-                    if (!is_geometry(zq)) { ++c_skip; continue; }
+                /* Front sample: l = s_f - p, its cosine to v, its sector coordinate.  The sample's
+                 * view ray is the centre pixel's ray plus the pixel offset over the focal length. */
+                const float aq = fmaf(dxf, c->inv_fx, ax), bq = fmaf(dyf, c->ninv_fy, by);
+                const float lx = fmaf(aq, zq, -px), ly = fmaf(bq, zq, -py), lz = z - zq;
+                const float dv = fmaf(lx, vx, fmaf(ly, vy, lz * vz));
+                const float ll = fmaf(lx, lx, fmaf(ly, ly, lz * lz));
+                ops += OPS_FRONT_COS;
+                /* Inside the edge band (cosine dv / sqrt(ll) below thr, compared through the
+                 * monotone map x -> x |x| without the square root): by the half-covered rule
+                 * (Section 3.1) the sample occludes nothing, because its back endpoint lies
+                 * still closer to that edge. */
+                if (dv * fabsf(dv) < thr2 * ll) continue;
+                float *e = ep ? ep + 2 * entry : NULL;
+                const float rl = orc32_rsqrt(ll);
+                const float cf = dv * rl;
+                const float Xf_raw = fmaf(orc32_acos(cf), sK, off);
+                const float Xf = fminf(fmaxf(Xf_raw, 0.0f), c->f_nb);
+                if (e) e[0] = Xf_raw;
+                ops += OPS_FRONT_ANGLE;
+                /* The same band in sector units (exact for the computed endpoint). */
+                if (pos ? Xf > c->edge_hi : Xf < c->edge_lo) continue;
 
-                    /* Front sample: l = s_f - p, its cosine to v, its sector coordinate.  The sample's
-                     * view ray is the centre pixel's ray plus the pixel offset over the focal length. */
-                    const float aq = fmaf(dxf, inv_fx, ax), bq = fmaf(dyf, ninv_fy, by);
-                    const float lx = fmaf(aq, zq, -px), ly = fmaf(bq, zq, -py), lz = z - zq;
-                    const float dv = fmaf(lx, vx, fmaf(ly, vy, lz * vz));
-                    const float ll = fmaf(lx, lx, fmaf(ly, ly, lz * lz));
-                    ops += OPS_FRONT_COS;
-                    /* Inside the edge band (cosine dv / sqrt(ll) below thr, compared through the
-                     * monotone map x -> x |x| without the square root): by the half-covered rule
-                     * (Section 3.1) the sample occludes nothing, because its back endpoint lies
-                     * still closer to that edge. */
-                    if (dv * fabsf(dv) < thr2 * ll) continue;
-                    uint8_t *tr = g_trace ? g_trace + (((size_t)pi * nd + i) * 2 + side) * ns + j : NULL;
-                    if (tr) *tr = 1;
-                    float *ep = g_endpoints ? g_endpoints + 2 * ((((size_t)pi * nd + i) * 2 + side) * ns + j) : NULL;
-                    const float rl = orc32_rsqrt(ll);
-                    const float cf = dv * rl;
-                    const float Xf_raw = fmaf(orc32_acos(cf), sK, off);
-                    const float Xf = fminf(fmaxf(Xf_raw, 0.0f), f_nb);
-                    if (ep) ep[0] = Xf_raw;
-                    ops += OPS_FRONT_ANGLE;
-                    /* The same band in sector units (exact for the computed endpoint). */
-                    if (pos ? Xf > edge_hi : Xf < edge_lo) continue;
-
-                    /* Back sample (constant thickness behind the front one). */
-                    float Xb;
-                    if (inf_t) {
-                        Xb = edge;
-                    } else {
-                        const float dvb = dv - tp;
-                        const float llb = fmaf(m2t, dv, ll + t2);
-                        const float cb = dvb * orc32_rsqrt(llb);
-                        const float Xb_raw = fmaf(orc32_acos(cb), sK, off);
-                        Xb = fminf(fmaxf(Xb_raw, 0.0f), f_nb);
-                        if (ep) ep[1] = Xb_raw;
-                        ops += OPS_BACK;
-                    }
-                    /* The back endpoint lies toward this side's edge: [A, B] = [X_f, X_b] on side +,
-                     * [X_b, X_f] on side - (a rounding-level reversal leaves B < A: no sector). */
-                    const float A = pos ? Xf : Xb, B = pos ? Xb : Xf;
-                    const mask_t bj = sector_run(A, B, nb, pb->hit_rule);
-                    const int newly = popc128(bj & ~b);
-                    b |= bj;
-                    ops += ops_run;
-
-                    /* Indirect light from the newly occluded sectors (Section 3.3). */
-                    if (newly > 0 && pb->gi) {
-                        ++c_gi;
-                        if (tr) *tr |= 2;
-                        const float *cj = pb->radiance + 4 * q, *nj = pb->normal + 4 * q;
-                        const float cp = fmaxf(fmaf(nx, lx, fmaf(ny, ly, nz * lz)) * rl, 0.0f);
-                        const float cq = fmaxf(-(fmaf(nj[0], lx, fmaf(nj[1], ly, nj[2] * lz)) * rl), 0.0f);
-                        const float wgt = (((float)newly * inv_nb) * cp) * cq;
-                        GIr = fmaf(wgt, cj[0], GIr);
-                        GIg = fmaf(wgt, cj[1], GIg);
-                        GIb = fmaf(wgt, cj[2], GIb);
-                        ops += OPS_GI;
-                    }
+                /* Back sample (constant thickness behind the front one). */
+                float Xb;
+                if (c->inf_t) {
+                    Xb = edge;
+                } else {
+                    const float dvb = dv - tp;
+                    const float llb = fmaf(m2t, dv, ll + t2);
+                    const float cb = dvb * orc32_rsqrt(llb);
+                    const float Xb_raw = fmaf(orc32_acos(cb), sK, off);
+                    Xb = fminf(fmaxf(Xb_raw, 0.0f), c->f_nb);
+                    if (e) e[1] = Xb_raw;
+                    ops += OPS_BACK;
                 }
-            }
-
-            /* Slice end: unoccluded fraction, then the ambient cones (Section 3.2). */
-            const int occ = popc128(b);
-            AO += (float)(nb - occ) * inv_nb;
-            ops += 5;
-            for (int k = 0; k < na; ++k) {
-                const int g = nb / na;
-                const mask_t Mk = low_bits((k + 1) * g) & ~low_bits(k * g);
-                const int freek = popc128(~b & Mk);
-                const float ck = fmaf(cg, ccos[k], -(sg * csin[k]));
-                const float sk = fmaf(sg, ccos[k], cg * csin[k]);
-                const float ax3 = fmaf(ck, vx, sk * sx), ay3 = fmaf(ck, vy, sk * sy), az3 = fmaf(ck, vz, sk * sz);
-                const float *R = pb->view_to_world;
-                const float wx = fmaf(R[0], ax3, fmaf(R[1], ay3, R[2] * az3));
-                const float wy = fmaf(R[3], ax3, fmaf(R[4], ay3, R[5] * az3));
-                const float wz = fmaf(R[6], ax3, fmaf(R[7], ay3, R[8] * az3));
-                float Y[9];
-                Y[0] = Y0;
-                Y[1] = Y1 * wy;
-                Y[2] = Y1 * wz;
-                Y[3] = Y1 * wx;
-                Y[4] = Y2 * (wx * wy);
-                Y[5] = Y2 * (wy * wz);
-                Y[6] = Y3 * fmaf(3.0f * wz, wz, -1.0f);
-                Y[7] = Y2 * (wx * wz);
-                Y[8] = Y4 * fmaf(wx, wx, -(wy * wy));
-                const float wt = (float)freek * inv_nb;
-                float L[3];
-                for (int c = 0; c < 3; ++c) {
-                    float acc = pb->sh[c] * Y[0];
-                    for (int m = 1; m < 9; ++m) acc = fmaf(pb->sh[3 * m + c], Y[m], acc);
-                    L[c] = acc;
+                /* The back endpoint lies toward this side's edge: [A, B] = [X_f, X_b] on side +,
+                 * [X_b, X_f] on side - (a rounding-level reversal leaves B < A: no sector). */
+                const float A = pos ? Xf : Xb, B = pos ? Xb : Xf;
+                int lo, hi;
+                const mask_t bj = sector_run(A, B, nb, pb->hit_rule, &lo, &hi);
+                if (runs && hi > lo) {
+                    runs[2 * entry] = (int16_t)lo;
+                    runs[2 * entry + 1] = (int16_t)hi;
                 }
-                AMr = fmaf(wt, L[0], AMr);
-                AMg = fmaf(wt, L[1], AMg);
-                AMb = fmaf(wt, L[2], AMb);
-                ops += ops_cone;
-            }
-            if (masks) {
-                masks[((size_t)pi * nd + i) * words] = (uint64_t)b;
-                if (words == 2) masks[((size_t)pi * nd + i) * words + 1] = (uint64_t)(b >> 64);
+                const int newly = popc128(bj & ~b);
+                b |= bj;
+                ops += c->ops_run;
+
+                /* Indirect light from the newly occluded sectors (Section 3.3). */
+                if (newly > 0 && pb->gi) {
+                    ++cnt[5];
+                    const float *cj = pb->radiance + 4 * q, *nj = pb->normal + 4 * q;
+                    const float cp = fmaxf(fmaf(nx, lx, fmaf(ny, ly, nz * lz)) * rl, 0.0f);
+                    const float cq = fmaxf(-(fmaf(nj[0], lx, fmaf(nj[1], ly, nj[2] * lz)) * rl), 0.0f);
+                    const float wgt = (((float)newly * c->inv_nb) * cp) * cq;
+                    GIr = fmaf(wgt, cj[0], GIr);
+                    GIg = fmaf(wgt, cj[1], GIg);
+                    GIb = fmaf(wgt, cj[2], GIb);
+                    ops += OPS_GI;
+                }
             }
         }
-        if (o0) { o0[0] = GIr * inv_nd; o0[1] = GIg * inv_nd; o0[2] = GIb * inv_nd; o0[3] = AO * inv_nd; }
-        if (o1) { o1[0] = AMr * inv_nd; o1[1] = AMg * inv_nd; o1[2] = AMb * inv_nd; o1[3] = 0.0f; }
-        ops += 8;
+
+        /* Slice end: unoccluded fraction, then the ambient cones (Section 3.2). */
+        const int occ = popc128(b);
+        AO += (float)(nb - occ) * c->inv_nb;
+        ops += 5;
+        for (int k = 0; k < na; ++k) {
+            const int g = nb / na;
+            const mask_t Mk = low_bits((k + 1) * g) & ~low_bits(k * g);
+            const int freek = popc128(~b & Mk);
+            const float ck = fmaf(cg, c->ccos[k], -(sg * c->csin[k]));
+            const float sk = fmaf(sg, c->ccos[k], cg * c->csin[k]);
+            const float ax3 = fmaf(ck, vx, sk * sx), ay3 = fmaf(ck, vy, sk * sy), az3 = fmaf(ck, vz, sk * sz);
+            const float *R = pb->view_to_world;
+            const float wx = fmaf(R[0], ax3, fmaf(R[1], ay3, R[2] * az3));
+            const float wy = fmaf(R[3], ax3, fmaf(R[4], ay3, R[5] * az3));
+            const float wz = fmaf(R[6], ax3, fmaf(R[7], ay3, R[8] * az3));
+            float Y[9];
+            Y[0] = c->Y0;
+            Y[1] = c->Y1 * wy;
+            Y[2] = c->Y1 * wz;
+            Y[3] = c->Y1 * wx;
+            Y[4] = c->Y2 * (wx * wy);
+            Y[5] = c->Y2 * (wy * wz);
+            Y[6] = c->Y3 * fmaf(3.0f * wz, wz, -1.0f);
+            Y[7] = c->Y2 * (wx * wz);
+            Y[8] = c->Y4 * fmaf(wx, wx, -(wy * wy));
+            const float wt = (float)freek * c->inv_nb;
+            float L[3];
+            for (int ch = 0; ch < 3; ++ch) {
+                float acc = pb->sh[ch] * Y[0];
+                for (int m = 1; m < 9; ++m) acc = fmaf(pb->sh[3 * m + ch], Y[m], acc);
+                L[ch] = acc;
+            }
+            AMr = fmaf(wt, L[0], AMr);
+            AMg = fmaf(wt, L[1], AMg);
+            AMb = fmaf(wt, L[2], AMb);
+            ops += c->ops_cone;
+        }
+        if (mk) {
+            mk[(size_t)i * words] = (uint64_t)b;
+            if (words == 2) mk[(size_t)i * words + 1] = (uint64_t)(b >> 64);
+        }
+    }
+    if (o0) { o0[0] = GIr * c->inv_nd; o0[1] = GIg * c->inv_nd; o0[2] = GIb * c->inv_nd; o0[3] = AO * c->inv_nd; }
+    if (o1) { o1[0] = AMr * c->inv_nd; o1[1] = AMg * c->inv_nd; o1[2] = AMb * c->inv_nd; o1[3] = 0.0f; }
+    cnt[6] += ops + 8;
+}
+
+int orc32_pixels_ex(const orc_problem *pb, int n, const int32_t *xy, float *out0, float *out1, uint64_t *masks,
+                    int64_t *counts, int16_t *runs, float *endpoints) {
+    int bad = validate(pb);
+    if (bad) return bad;
+    if (n < 0 || (n > 0 && !xy)) return 10;
+    for (int pi = 0; pi < n; ++pi)
+        if (xy[2 * pi] < 0 || xy[2 * pi + 1] < 0 || xy[2 * pi] >= pb->width || xy[2 * pi + 1] >= pb->height) return 10;
+    ctx32 c;
+    setup32(pb, &c);
+    const size_t per_pixel = (size_t)c.nd * 2 * c.ns; /* entries of the run and endpoint blocks */
+    int64_t c0 = 0, c1 = 0, c2 = 0, c3 = 0, c4 = 0, c5 = 0, c6 = 0;
+    /* Pixels are independent and each writes only its own outputs, so the result does not depend
+     * on how the loop is split over threads; the counters are integer sums. */
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : c0, c1, c2, c3, c4, c5, c6)
+    for (int pi = 0; pi < n; ++pi) {
+        int64_t cnt[7] = {0, 0, 0, 0, 0, 0, 0};
+        pixel32(pb, &c, xy[2 * pi], xy[2 * pi + 1], out0 ? out0 + 4 * (size_t)pi : NULL,
+                out1 ? out1 + 4 * (size_t)pi : NULL, masks ? masks + (size_t)pi * c.nd * c.words : NULL, cnt,
+                runs ? runs + 2 * per_pixel * pi : NULL, endpoints ? endpoints + 2 * per_pixel * pi : NULL);
+        c0 += cnt[0]; c1 += cnt[1]; c2 += cnt[2]; c3 += cnt[3]; c4 += cnt[4]; c5 += cnt[5]; c6 += cnt[6];
     }
     if (counts) {
-        counts[0] = c_pix; counts[1] = c_sky; counts[2] = c_slice; counts[3] = c_visit;
-        counts[4] = c_skip; counts[5] = c_gi; counts[6] = ops;
+        counts[0] = c0; counts[1] = c1; counts[2] = c2; counts[3] = c3;
+        counts[4] = c4; counts[5] = c5; counts[6] = c6;
     }
     return 0;
+}
+
+int orc32_pixels(const orc_problem *pb, int n, const int32_t *xy, float *out0, float *out1, uint64_t *masks,
+                 int64_t *counts) {
+    return orc32_pixels_ex(pb, n, xy, out0, out1, masks, counts, NULL, NULL);
 }
 
 /* Test helper: sweep every binary32 value in [0, 1] (bit patterns 0 .. 0x3f800000).

@@ -1,16 +1,19 @@
 """Helpers shared by the GPU tests: run the CUDA gather through the C ABI and compare
 it with the CPU oracle.
 
-Gates: (G1) bitmasks bit-exact against the binary32 replica.  (G3) Every FP64/binary32 mask
-disagreement is explained by an FP64 decision that lies within the binary32 error bound of its
-endpoints from its rounding boundary (the oracle's ratio <= 1; the bound grows where an angle is
-taken from a cosine near +-1 and where a sample lies close to the centre point).  (G2) AO, GI
-and ambient within 1e-4 of the FP64 oracle on every pixel whose masks agree and all of whose
-hit-rule decisions lie beyond that bound (ratio > 1): there both precisions take the same
-decisions, so the outputs differ by rounding only.  On the remaining pixels the two precisions
-may credit a sector to a different sample (GI credits each sector to the first sample that
-covers it) or flip it: there the difference is bounded by a few sectors' share.  (G4) The mean
-absolute error against FP64 over every compared pixel is at most 1e-4."""
+Gates: (G1) bitmasks bit-exact against the binary32 replica.  (G2) AO, GI and ambient within 1e-4
+of the decision-forced FP64 evaluation on EVERY compared pixel: the FP64 oracle evaluated on the
+replica's per-sample sector runs (the integer decisions the GPU must share), with the geometry,
+cosines, crediting and ambient cones in FP64.  (G2c) The same 1e-4 against the free-running FP64
+oracle on every pixel whose masks agree and all of whose hit-rule decisions lie beyond the binary32
+error bound of their endpoints (the oracle's ratio > 1): there both precisions take the same
+decisions.  (G3) Every FP64/binary32 mask disagreement is explained by an FP64 decision that lies
+within the binary32 error bound of its endpoints from its rounding boundary (ratio <= 1; the bound
+grows where an angle is taken from a cosine near +-1 and where a sample lies close to the centre
+point).  (G4) The mean absolute error against the free-running FP64 oracle over every compared pixel
+is at most 1e-4.  Elsewhere the two precisions may credit a sector to a different sample (GI
+credits each sector to the first sample that covers it) or flip it; G2 checks those pixels against
+FP64 arithmetic on the binary32 decisions."""
 import numpy as np
 
 import oracle
@@ -81,9 +84,18 @@ def check_parity(g, prm, noise, sh, gpu, pixels=None, min_agree=0.98, gathered=F
         g0, g1, gm = gpu[0][idx], pick(gpu[1], idx), gpu[2][idx]
     r0, r1, rm = oracle.fp32(prob, xy)
     e0, e1, em, margin, ratio = oracle.fp64(prob, xy, ratio=True)
+    f0, f1, fm, _ = oracle.fp64(prob, xy, forced=True)
     # G1: bitmasks bit-exact against the binary32 replica
     bad = np.argwhere(gm != rm)
     assert bad.size == 0, f"{len(bad)} bitmasks differ from the replica, first at pixel {xy[bad[0][0]]}"
+    assert np.array_equal(fm, rm), "the forced evaluation must take the replica's decisions"
+    # G2: every pixel within 1e-4 of FP64 arithmetic on the binary32 decisions
+    ferr0 = np.abs(g0 - f0).max(initial=0.0)
+    assert ferr0 <= TOL, f"out0 off the decision-forced FP64 evaluation by {ferr0}"
+    ferr1 = 0.0
+    if prm.ambient_cones > 0:
+        ferr1 = np.abs(g1 - f1).max(initial=0.0)
+        assert ferr1 <= TOL, f"out1 off the decision-forced FP64 evaluation by {ferr1}"
     # G3: FP64 vs binary32 mask disagreements only within the binary32 error bound of a boundary
     diff = em != rm
     if diff.ndim == 3:
@@ -91,10 +103,10 @@ def check_parity(g, prm, noise, sh, gpu, pixels=None, min_agree=0.98, gathered=F
     assert np.all(ratio[diff] <= 1.0), f"unexplained mask flip, distance / error bound {ratio[diff].max()}"
     agree = ~diff.any(axis=1)
     assert agree.mean() >= min_agree, agree.mean()
-    # G2: continuous outputs within 1e-4 of FP64 where every decision lies beyond its binary32
-    # error bound.  The bound is conservative (measured endpoint errors stay below a sixth of it),
-    # so fewer pixels qualify at N_b = 128 and for the floor/ceil rule, which flips on samples lying
-    # in the tangent plane to rounding; the floor only guards against a vacuous comparison.
+    # G2c: against the free-running FP64 oracle where every decision lies beyond its binary32 error
+    # bound.  The bound is conservative (measured endpoint errors stay below a sixth of it), so fewer
+    # pixels qualify at N_b = 128 and for the floor/ceil rule, which flips on samples lying in the
+    # tangent plane to rounding; the floor only guards against a vacuous comparison.
     clear = agree & (ratio.min(axis=1) > 1.0)
     assert clear.mean() >= (0.75 if prm.hit_rule == 0 else 0.6), clear.mean()
     err0 = np.abs(g0[clear] - e0[clear]).max(initial=0.0)
@@ -102,14 +114,9 @@ def check_parity(g, prm, noise, sh, gpu, pixels=None, min_agree=0.98, gathered=F
     if prm.ambient_cones > 0:
         err1 = np.abs(g1[clear] - e1[clear]).max(initial=0.0)
         assert err1 <= TOL, err1
-    # near-boundary pixels: at most a few sectors' share (radiance and cosines are <= 1)
-    near = ~clear
-    few = 4.0 / prm.sector_count + TOL
-    assert np.abs(g0[near] - e0[near]).max(initial=0.0) <= few
-    if prm.ambient_cones > 0:
-        assert np.abs(g1[near] - e1[near]).max(initial=0.0) <= 2.0 * few
-    # G4: the mean error over every compared pixel, near-boundary ones included
-    mean0 = float(np.abs(g0 - e0).mean())
+    # G4: the mean error against the free-running FP64 oracle over every compared pixel
+    all0 = np.abs(g0 - e0)
+    mean0 = float(all0.mean()) if all0.size else 0.0
     assert mean0 <= TOL, mean0
     if prm.ambient_cones > 0:
         assert float(np.abs(g1 - e1).mean()) <= TOL
@@ -117,8 +124,14 @@ def check_parity(g, prm, noise, sh, gpu, pixels=None, min_agree=0.98, gathered=F
     assert np.abs(g0 - r0).max(initial=0.0) <= 1e-6
     if prm.ambient_cones > 0:
         assert np.abs(g1 - r1).max(initial=0.0) <= 1e-6
+    # reported, not gated: the largest difference from the free-running FP64 oracle over all pixels
+    # and the share of pixels above 1e-4 (decisions within rounding of a boundary moved a sector)
+    worst = all0.max(axis=1) if all0.size else np.zeros(0)
+    if prm.ambient_cones > 0 and all0.size:
+        worst = np.maximum(worst, np.abs(g1 - e1).max(axis=1))
     return {"agree": float(agree.mean()), "clear": float(clear.mean()), "err_fp64": float(err0), "mean_err_fp64": mean0,
-            "n": len(xy)}
+            "err_forced": float(max(ferr0, ferr1)), "max_err_fp64_all": float(worst.max(initial=0.0)),
+            "share_above_tol": float((worst > TOL).mean()) if worst.size else 0.0, "n": len(xy)}
 
 
 def sample_pixels(H, W, n, seed=0):

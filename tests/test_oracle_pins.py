@@ -640,3 +640,111 @@ def test_binary32_endpoints_within_the_error_bound(seed, W, H, kw):
         assert np.all(np.abs(x32[ok] - x64[ok]) <= bound[ok]), np.max(np.abs(x32[ok] - x64[ok]) / bound[ok])
         assert np.median(bound[ok]) < 0.05 * prm.sector_count / 32
     assert n > 100000
+
+
+# --- the decision-forced FP64 evaluation (GPU gate on every pixel) ----------------------------
+
+FORCED_CASES = [
+    (1, 256, 256, dict(num_slices=4, steps_per_side=8, radius=2.0, thickness=0.5), True),
+    (15, 64, 48, dict(num_slices=3, steps_per_side=12, sector_count=128, ambient_cones=8), True),
+    (14, 33, 70, dict(num_slices=4, steps_per_side=10, sector_count=64, step_mode=1, ambient_cones=4), True),
+    (16, 45, 37, dict(num_slices=2, steps_per_side=9, sector_count=128, thickness=INF, hit_rule=1), True),
+    (10, 64, 48, dict(num_slices=2, steps_per_side=8, thickness=0.1, thickness_slope=0.05), False),
+]
+
+
+def _forced_problem(seed, W, H, kw, use_noise):
+    g = scenegen.render(seed, W, H, 8, 3)
+    prm = Params(**kw)
+    sh = scenegen.sh_environment(7) if prm.ambient_cones else None
+    return oracle.Problem(g, prm, scenegen.ign_table() if use_noise else None, sh), prm
+
+
+@pytest.mark.parametrize("seed,W,H,kw,use_noise", FORCED_CASES)
+def test_forced_evaluation_equals_free_running_fp64_where_decisions_agree(seed, W, H, kw, use_noise):
+    """The forced evaluation takes the replica's sector run for every sample and keeps everything
+    else in FP64 (Algorithm 1; Section 3.3 crediting).  Where every FP64 decision lies beyond its
+    binary32 error bound the two decide alike, so there it must reproduce the free-running oracle
+    to 1e-12; on every pixel its masks must be the replica's and its outputs within binary32
+    rounding of the replica's (the same decisions, arithmetic in two precisions)."""
+    prob, prm = _forced_problem(seed, W, H, kw, use_noise)
+    e0, e1, em, _, ratio = oracle.fp64(prob, ratio=True)
+    f0, f1, fm, _ = oracle.fp64(prob, forced=True)
+    r0, r1, rm = oracle.fp32(prob)
+    assert np.array_equal(fm, rm)
+    same = (em == rm) if em.ndim == 2 else (em == rm).all(axis=2)
+    clear = same.all(axis=1) & (ratio.min(axis=1) > 1.0)
+    assert clear.mean() > 0.6
+    assert np.abs(f0[clear] - e0[clear]).max() <= 1e-12
+    assert np.abs(f1[clear] - e1[clear]).max() <= 1e-12
+    assert np.abs(f0 - r0).max() <= 1e-5 and np.abs(f1 - r1).max() <= 1e-5
+    # not vacuous where it matters: some pixels are not clear, and there the forced evaluation
+    # follows the replica's decisions rather than the free-running oracle's
+    if not clear.all():
+        assert np.abs(f0[~clear] - r0[~clear]).max() <= 1e-5
+
+
+def test_replica_runs_make_up_its_masks():
+    """The per-sample runs the forced evaluation consumes are the replica's: OR-ing a slice's runs
+    gives its mask, and every run lies inside [0, N_b]."""
+    prob, prm = _forced_problem(15, 64, 48, dict(num_slices=3, steps_per_side=12, sector_count=128,
+                                                 ambient_cones=8), True)
+    runs = oracle.runs32(prob).astype(np.int64)
+    _, _, rm = oracle.fp32(prob)
+    lo, hi = runs[..., 0], runs[..., 1]
+    assert np.all((hi <= lo) | ((lo >= 0) & (hi <= 128)))
+    assert (hi > lo).sum() > 1000
+    k = np.arange(128)
+    cover = ((k >= lo[..., None]) & (k < hi[..., None])).any(axis=(2, 3))  # [n, N_d, 128]
+    words = np.zeros(rm.shape, dtype=np.uint64)
+    for w in range(2):
+        bits = cover[..., 64 * w:64 * (w + 1)].astype(np.uint64) << np.arange(64, dtype=np.uint64)
+        words[..., w] = np.bitwise_or.reduce(bits, axis=-1)
+    assert np.array_equal(words, rm)
+
+
+def test_forced_empty_runs_give_full_visibility():
+    """Forcing every run empty leaves nothing occluded: AO = 1 and GI = 0 exactly, and with a
+    constant (band-0) environment every cone sees its full sector share, so the ambient is the
+    constant radiance c_00 Y_00 (Section 3.2)."""
+    import ctypes
+    g = scenegen.render(12, 40, 30, 8, 3)
+    prm = Params(num_slices=3, steps_per_side=8, ambient_cones=4)
+    sh = np.zeros((9, 3), dtype=np.float32)
+    sh[0] = [0.9, 0.6, 0.3]
+    prob = oracle.Problem(g, prm, scenegen.ign_table(), sh)
+    xy = oracle.all_pixels(30, 40)
+    n = len(xy)
+    o0 = np.zeros((n, 4)); o1 = np.zeros((n, 4)); m = np.zeros((n, 3), dtype=np.uint64)
+    runs = np.zeros((n, 3, 2, 8, 2), dtype=np.int16)
+    rc = oracle.lib().orc64_pixels_ex(ctypes.byref(prob.c), n, xy.ctypes.data, o0.ctypes.data, o1.ctypes.data,
+                                      m.ctypes.data, None, None, runs.ctypes.data, None)
+    assert rc == 0
+    assert np.all(m == 0) and np.all(o0[:, 3] == 1.0) and np.all(o0[:, :3] == 0.0)
+    geo = np.isfinite(g.depth.reshape(-1)) & (g.depth.reshape(-1) > 0)
+    expect = sh[0].astype(np.float64) * 0.5 * math.sqrt(1.0 / math.pi)
+    np.testing.assert_allclose(o1[geo, :3], np.broadcast_to(expect, (geo.sum(), 3)), rtol=1e-12)
+    bad = runs.copy()
+    bad[0, 0, 0, 0] = (3, 200)  # a run beyond N_b is rejected
+    assert oracle.lib().orc64_pixels_ex(ctypes.byref(prob.c), n, xy.ctypes.data, None, None, None, None, None,
+                                        bad.ctypes.data, None) == 11
+
+
+def test_results_do_not_depend_on_the_thread_count():
+    """Pixels are independent; the OpenMP pixel loops must give the same bits on 1 thread and on
+    all of them (outputs, masks, counters, runs)."""
+    prob, prm = _forced_problem(14, 33, 70, dict(num_slices=4, steps_per_side=10, sector_count=64, step_mode=1,
+                                                 ambient_cones=4), True)
+    full = oracle.threads()
+    try:
+        res = []
+        for t in (1, max(full, 2)):
+            oracle.threads(t)
+            res.append((oracle.fp32(prob, counts=True), oracle.fp64(prob, ratio=True), oracle.runs32(prob),
+                        oracle.fp64(prob, forced=True)))
+    finally:
+        oracle.threads(full)
+    (a32, a64, ar, af), (b32, b64, br, bf) = res
+    for x, y in zip(a32[:3] + a64 + af, b32[:3] + b64 + bf):
+        assert np.array_equal(x, y)
+    assert a32[3] == b32[3] and np.array_equal(ar, br)
