@@ -102,7 +102,17 @@ typedef struct {
                               1: quadratic ("exponential") steps r ((j+1+xi_s)/(N_s+1))^2 */
     int ambient_cones;     /* N_a in {0, 1, 2, 4, 8} dividing N_b: ambient cones per slice, 0 = off */
     int compute_gi;        /* 1 = indirect diffuse (reads normal and radiance at samples), 0 = off */
-    const float *noise_table; /* HOST, 16 x (xi_phi, xi_s) in [0,1), row (y&3)*4 + (x&3); NULL = zeros */
+    int noise_mode;        /* per-pixel slice rotation xi_phi and step jitter xi_s ("directions with random
+                              offset", Section 3.1; spatial and temporal jitter, Section 4.3), one pair per
+                              4x4 pixel class, row (y&3)*4 + (x&3):
+                              0 = none (both 0);
+                              1 = built in: xi_phi = Jimenez's interleaved gradient noise at the class's
+                                  pixel offset by 5.588238 (noise_frame mod 64) pixels along x and y,
+                                  xi_s = frac(xi_phi + 1/2), each computed in FP64 and rounded to binary32
+                                  once (a value that rounds to 1 becomes 0);
+                              2 = the caller's noise_table */
+    int noise_frame;       /* noise_mode 1: frame index of the temporal rotation (>= 0) */
+    const float *noise_table; /* HOST, noise_mode 2 only (else NULL): 16 x (xi_phi, xi_s) in [0,1) */
     const float *sh_rgb;   /* HOST, 9 x 3 real SH radiance coefficients [m][rgb] of the ambient
                               environment (order Y00, Y1-1, Y10, Y11, Y2-2, Y2-1, Y20, Y21, Y22);
                               required iff ambient_cones > 0 */
@@ -143,7 +153,8 @@ typedef enum {
 typedef struct {
     int mapping;          /* ssilvb_mapping, single-frame calls */
     int occupancy;        /* 0 (default: 8 for N_b 32, else 9), or 8 / 9: blocks of 128 threads per SM the register budget is sized for */
-    int rows_per_tile;    /* batch: 0, or 1..8 image rows per work item */
+    int rows_per_tile;    /* batch: 0, or 1..8 patch rows per work item (a patch row is 16 pixel rows of
+                             one 32-pixel-wide patch column, one row class of 4) */
     int ctas_per_sm;      /* batch: 0 (as many as fit), or 1..16 blocks per SM in the persistent grid */
     int use_graph;        /* batch, persistent mode: 0 auto, 1 launch through a cached CUDA graph, 2 plain */
     int batch_mode;       /* batch: 0 auto, 1 one persistent kernel over a tile queue,
@@ -215,10 +226,11 @@ ssilvb_status ssilvb_gather_host_async(ssilvb_ctx *ctx, const ssilvb_gbuffer *gb
  * the size, the camera and the noise may differ per frame.  Output regions of different frames
  * must not overlap.  Each frame's results are bit-identical to an ssilvb_gather of that frame.
  * Two launch forms (ssilvb_tuning.batch_mode; the autotuner picks): (1) one persistent kernel:
- * work items are bands of rows_per_tile rows x 128 pixels, concatenated over the frames and
- * handed to the resident blocks through a queue counter the context owns, launched through a
- * CUDA graph the context caches; (2) one CUDA graph whose independent nodes are the frames'
- * kernels, so the frames run concurrently.  Asynchronous on stream.  The context keeps up to 4
+ * a work item is rows_per_tile patch rows (16 pixel rows each) of one 32-pixel-wide patch column
+ * and one of its 4 row classes (a block of 128 threads, each warp 8 x 4 pixels at stride 4);
+ * the items of all frames are concatenated and handed to the resident blocks through a queue
+ * counter the context owns, launched through a CUDA graph the context caches; (2) one CUDA graph
+ * whose independent nodes are the frames' kernels, so the frames run concurrently.  Asynchronous on stream.  The context keeps up to 4
  * batches in flight; a call that needs a busy slot first waits on the host for that slot's
  * previous batch.  1 <= n_frames <= 4096; frames is host memory read during the call. */
 ssilvb_status ssilvb_gather_batch(ssilvb_ctx *ctx, const ssilvb_frame *frames, int n_frames,
@@ -234,8 +246,7 @@ ssilvb_status ssilvb_autotune(ssilvb_ctx *ctx, const ssilvb_frame *frames, int n
 
 /* The batch gather of ssilvb_gather_batch (persistent-kernel form) for callers that cannot
  * allocate device memory when they call it: an engine that reserves its whole GPU budget up
- * front and forbids driver allocations in its frame loop, code running while a global-mode
- * stream capture is active (cudaMalloc is illegal there), or a plug-in whose host application
+ * front and forbids driver allocations in its frame loop, or a plug-in whose host application
  * owns all device memory; cudaMalloc also synchronises the device, which a real-time loop
  * cannot afford.  The paper has no counterpart: this is an interface choice only.
  * No context: it runs on the CURRENT device, and its scratch (the work list and the tile-queue
@@ -244,9 +255,13 @@ ssilvb_status ssilvb_autotune(ssilvb_ctx *ctx, const ssilvb_frame *frames, int n
  * cudaFree, graph or event); the caller still passes all inputs and outputs, with the same
  * rules as ssilvb_gather_batch.  At most 16 frames (INVALID_ARG beyond, with the limit in the
  * message).  The first call on a device looks up the array's device address (and loads the
- * kernels if CUDA loads modules lazily), so make it before any stream capture.  Every call
- * shares the array and overwrites the previous call's work list: calls whose work overlaps on
- * the GPU race and give wrong results, so issue them on one stream or order them.
+ * kernels if CUDA loads modules lazily), so make it before any stream capture.  The work list
+ * is uploaded from host memory on the calling thread's stack with cudaMemcpyAsync.  Every call
+ * shares the array and overwrites the previous call's work list and counter.  Calls whose work
+ * overlaps on the GPU therefore race: a running kernel can read another call's frame table,
+ * mixing one frame's sizes and pitches with another frame's pointers, and so read and write
+ * out of the bounds of any buffer passed in.  The caller must order the calls: issue them on
+ * one stream, or make each wait for the previous one with an event.
  * Asynchronous on stream; the host frame array is read during the call only.  Error detail:
  * ssilvb_last_error(NULL) in the calling thread. */
 ssilvb_status ssilvb_gather_batch_noalloc(const ssilvb_frame *frames, int n_frames, struct CUstream_st *stream);

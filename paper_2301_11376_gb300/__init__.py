@@ -89,7 +89,8 @@ class ParamsC(ctypes.Structure):
     _fields_ = [("num_slices", ctypes.c_int), ("steps_per_side", ctypes.c_int), ("radius", ctypes.c_float),
                 ("thickness", ctypes.c_float), ("thickness_slope", ctypes.c_float), ("sector_count", ctypes.c_int),
                 ("hit_rule", ctypes.c_int), ("step_mode", ctypes.c_int), ("ambient_cones", ctypes.c_int),
-                ("compute_gi", ctypes.c_int), ("noise_table", ctypes.c_void_p), ("sh_rgb", ctypes.c_void_p),
+                ("compute_gi", ctypes.c_int), ("noise_mode", ctypes.c_int), ("noise_frame", ctypes.c_int),
+                ("noise_table", ctypes.c_void_p), ("sh_rgb", ctypes.c_void_p),
                 ("bounce_gain", ctypes.c_float)]
 
 
@@ -201,7 +202,17 @@ def _params_c(p, keep: _HostArrays, noise=None, sh=None) -> ParamsC:
     c.step_mode = int(getattr(p, "step_mode", 0))
     c.ambient_cones = int(p.ambient_cones)
     c.compute_gi = 1 if getattr(p, "gi", True) else 0
-    c.noise_table = keep.ptr(noise, 32)
+    # noise: None (mode 0), "ign" or ("ign", frame) (mode 1, the library's built-in table), or a
+    # 16 x 2 table (mode 2)
+    if noise is None:
+        c.noise_mode, c.noise_frame, c.noise_table = 0, 0, None
+    elif isinstance(noise, str) or (isinstance(noise, tuple) and noise and isinstance(noise[0], str)):
+        name, frame = (noise, 0) if isinstance(noise, str) else noise
+        if name != "ign":
+            raise ValueError(f"unknown built-in noise {name!r}")
+        c.noise_mode, c.noise_frame, c.noise_table = 1, int(frame), None
+    else:
+        c.noise_mode, c.noise_frame, c.noise_table = 2, 0, keep.ptr(noise, 32)
     c.sh_rgb = keep.ptr(sh, 27) if (sh is not None and p.ambient_cones > 0) else None
     c.bounce_gain = float(getattr(p, "bounce_gain", 0.0))
     return c

@@ -2,13 +2,13 @@
 //
 // Some callers cannot allocate GPU memory at the point where they want to run the gather:
 // a renderer or engine that reserves its whole device-memory budget up front and forbids
-// driver allocations inside the frame loop, code that runs while a CUDA stream capture is
-// active (cudaMalloc is not allowed during a global-mode capture), or a plug-in hosted by an
-// application that owns all device memory.  cudaMalloc also synchronises the device, which a
-// real-time frame loop cannot afford.  For them this entry point keeps the persistent kernel's
-// scratch (its work list and tile-queue counter) in a fixed array that lives in the library
-// image itself, so a call allocates nothing: no context, no cudaMalloc, no cudaFree, no
-// graph, no event.
+// driver allocations inside the frame loop, or a plug-in hosted by an application that owns
+// all device memory.  cudaMalloc also synchronises the device, which a real-time frame loop
+// cannot afford.  For them this entry point keeps the persistent kernel's scratch (its work
+// list and tile-queue counter) in a fixed array that lives in the library image itself, so a
+// call allocates nothing: no context, no cudaMalloc, no cudaFree, no graph, no event.  Calls
+// share that array, so the caller must order them (one stream, or an event between them);
+// calls that overlap on the GPU can mix frame tables and access memory out of bounds.
 #include <cuda_runtime.h>
 
 #include <algorithm>

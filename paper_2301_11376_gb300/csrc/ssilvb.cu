@@ -85,7 +85,16 @@ ssilvb_status validate(ssilvb_ctx *ctx, const ssilvb_gbuffer *g, const ssilvb_ca
     if (na != 0 && na != 1 && na != 2 && na != 4 && na != 8)
         return fail(ctx, SSILVB_ERR_INVALID_ARG, "ambient_cones %d not in {0,1,2,4,8}", na);
     if (na > 0 && !p->sh_rgb) return fail(ctx, SSILVB_ERR_INVALID_ARG, "sh_rgb required when ambient_cones > 0");
-    if (p->noise_table)
+    if (p->noise_mode < 0 || p->noise_mode > 2)
+        return fail(ctx, SSILVB_ERR_INVALID_ARG, "noise_mode %d not in {0, 1, 2}", p->noise_mode);
+    if (p->noise_mode == 2 && !p->noise_table)
+        return fail(ctx, SSILVB_ERR_INVALID_ARG, "noise_mode 2 needs noise_table");
+    if (p->noise_mode != 2 && p->noise_table)
+        return fail(ctx, SSILVB_ERR_INVALID_ARG, "noise_table is read only with noise_mode 2 (got mode %d)",
+                    p->noise_mode);
+    if (p->noise_mode == 1 && p->noise_frame < 0)
+        return fail(ctx, SSILVB_ERR_INVALID_ARG, "noise_frame %d must be >= 0", p->noise_frame);
+    if (p->noise_mode == 2)
         for (int i = 0; i < 32; ++i)
             if (!(p->noise_table[i] >= 0.0f && p->noise_table[i] < 1.0f))
                 return fail(ctx, SSILVB_ERR_INVALID_ARG, "noise_table[%d] not in [0, 1)", i);
@@ -128,6 +137,24 @@ ssilvb_status validate(ssilvb_ctx *ctx, const ssilvb_gbuffer *g, const ssilvb_ca
         }
     }
     return SSILVB_OK;
+}
+
+// The built-in noise table (noise_mode 1): per 4x4 pixel class, xi_phi = interleaved gradient
+// noise (Jimenez, "Next Generation Post Processing in Call of Duty: Advanced Warfare", SIGGRAPH
+// 2014), IGN(x, y) = frac(52.9829189 frac(0.06711056 x + 0.00583715 y)), at the class's pixel
+// offset by 5.588238 (frame mod 64) pixels along both axes for temporal variation, and
+// xi_s = frac(xi_phi + 1/2); FP64, each rounded once to binary32, a value that rounds to 1 taken as 0.
+static void builtin_noise(int frame, float table[32]) {
+    const double off = 5.588238 * (double)(frame % 64);
+    for (int y = 0; y < 4; ++y)
+        for (int x = 0; x < 4; ++x) {
+            const double px = x + off, py = y + off;
+            const double f = std::fmod(0.06711056 * px + 0.00583715 * py, 1.0);
+            const double xi = std::fmod(52.9829189 * f, 1.0);
+            float a = (float)xi, b = (float)std::fmod(xi + 0.5, 1.0);
+            table[2 * (y * 4 + x)] = a >= 1.0f ? 0.0f : a;
+            table[2 * (y * 4 + x) + 1] = b >= 1.0f ? 0.0f : b;
+        }
 }
 
 // Per-launch constants.  Every expression is written out exactly as the method's binary32
@@ -182,9 +209,12 @@ void fill_params(ssilvb::GatherParams &P, const ssilvb_gbuffer *g, const ssilvb_
     P.cdel = (float)std::cos(del);
     P.t0 = p->thickness;
     P.kt = p->thickness_slope;
+    float noise[32] = {};
+    if (p->noise_mode == 1) builtin_noise(p->noise_frame, noise);
+    else if (p->noise_mode == 2) std::memcpy(noise, p->noise_table, sizeof(noise));
     for (int cl = 0; cl < 16; ++cl) {
-        const float xi_phi = p->noise_table ? p->noise_table[2 * cl] : 0.0f;
-        P.xi_s[cl] = p->noise_table ? p->noise_table[2 * cl + 1] : 0.0f;
+        const float xi_phi = noise[2 * cl];
+        P.xi_s[cl] = noise[2 * cl + 1];
         for (int i = 0; i < nd; ++i) {
             const double phi = ((double)i + (double)xi_phi) * M_PI / (double)nd;
             P.dcos[cl][i] = (float)std::cos(phi);

@@ -4,18 +4,29 @@ Requests name a G-buffer that stays resident on the device and carry their own p
 (slices, steps, sector count ...).  The loop admits arrived requests into the next batch as
 soon as an in-flight slot and output memory are free, launches each batch with
 ``ssilvb_gather_batch`` on one of several streams (so batches overlap on the GPU), and
-records each request's completion on the device clock.  Output memory comes from one
-device arena with a first-fit free list; a request waits while its outputs do not fit.  The
-bound on the system counts every admitted request not yet complete, queued or on the GPU;
-arrivals beyond it are shed and counted.
+takes each request's completion time on the host clock when it first sees the batch's event
+complete.  Output memory comes from one device arena with a first-fit free list; a request
+waits while its outputs do not fit.  Requests of one batch share what ``ssilvb_gather_batch``
+requires them to share: sector count, storage format, infinite or finite thickness and step
+mode.
+
+Admission (``LatencyAdmission``): an arriving request is admitted only if its predicted
+latency fits a stated budget.  The prediction is first-in first-out service at a measured
+rate: the time it has already waited, plus the predicted time of all admitted, unfinished
+work, plus its own work (samples = 2 N_d N_s per pixel), divided by the rate, which starts
+from a calibration and follows completed work.  A request predicted to miss the budget is
+shed at arrival and counted.  Without a budget, a flat bound on the requests in the system
+(queued or on the GPU) sheds arrivals beyond it.
 
 ``PlainServer`` is the naive baseline: one request at a time, one ``ssilvb_gather`` launch
-and one host synchronisation per request, same queue bound.
+and one host synchronisation per request, under the same admission rule and the same
+host-side completion clock.
 """
 from __future__ import annotations
 
 import bisect
 import collections
+import math
 import time
 from dataclasses import dataclass, field
 
@@ -35,7 +46,9 @@ class Request:
 @dataclass
 class Stats:
     served: int = 0
-    dropped: int = 0
+    dropped: int = 0        # shed at arrival (predicted to miss the budget, or beyond the bound)
+    within_budget: int = 0  # served with latency <= budget (all served when there is no budget)
+    budget_ms: float | None = None
     latencies_ms: list = field(default_factory=list)
     wall_s: float = 0.0
     batches: int = 0
@@ -44,12 +57,58 @@ class Stats:
 
     def summary(self):
         lat = np.asarray(self.latencies_ms) if self.latencies_ms else np.zeros(1)
-        return {"served": self.served, "dropped": self.dropped,
+        return {"served": self.served, "shed": self.dropped, "within_budget": self.within_budget,
+                "budget_ms": self.budget_ms,
                 "frames_per_s": self.served / self.wall_s if self.wall_s > 0 else 0.0,
+                "goodput_frames_per_s": self.within_budget / self.wall_s if self.wall_s > 0 else 0.0,
                 "gsamples_per_s": self.samples / self.wall_s / 1e9 if self.wall_s > 0 else 0.0,
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                "mean_ms": float(lat.mean()), "batches": self.batches,
+                "max_ms": float(lat.max()), "mean_ms": float(lat.mean()), "batches": self.batches,
                 "max_batches_in_flight": self.max_inflight_seen, "wall_s": self.wall_s}
+
+
+def request_samples(H, W, prm):
+    """Samples of one request: 2 N_d N_s per pixel."""
+    return H * W * 2 * prm.num_slices * prm.steps_per_side
+
+
+class LatencyAdmission:
+    """Admission by predicted completion time under first-in first-out service.
+
+    budget_s: the latency budget (None: no latency test); max_in_system: a bound on the admitted
+    requests not yet complete (None: no bound).
+    rate: predicted service rate in samples/s (a calibration); observe() moves it toward the
+    rate of completed work (exponential average with weight alpha).
+    A request of `samples` that arrived at `arrival` is admitted at time `now` iff
+        (now - arrival) + (backlog + samples) / rate <= budget_s,
+    backlog being the samples of every admitted request not yet complete."""
+
+    def __init__(self, budget_s=None, rate=4e11, alpha=0.2, max_in_system=256):
+        self.budget_s, self.rate, self.alpha, self.max_in_system = budget_s, float(rate), alpha, max_in_system
+        self.backlog = 0
+        self.in_system = 0
+
+    def predicted_latency(self, now, arrival, samples):
+        return (now - arrival) + (self.backlog + samples) / self.rate
+
+    def admit(self, now, arrival, samples):
+        ok = self.max_in_system is None or self.in_system < self.max_in_system
+        if ok and self.budget_s is not None:
+            ok = self.predicted_latency(now, arrival, samples) <= self.budget_s
+        if ok:
+            self.backlog += samples
+            self.in_system += 1
+        return ok
+
+    def done(self, samples):
+        self.backlog -= samples
+        self.in_system -= 1
+
+    def observe(self, samples, service_s):
+        """Completed work: `samples` took `service_s` of service (time since the later of its start and
+        the previous completion)."""
+        if service_s > 0 and samples > 0:
+            self.rate = (1.0 - self.alpha) * self.rate + self.alpha * (samples / service_s)
 
 
 class ResidentPool:
@@ -113,59 +172,72 @@ def _out_bytes(H, W, prm):
     return H * W * 16 * (2 if prm.ambient_cones > 0 else 1)
 
 
+def _batch_key(pool, req):
+    """What the frames of one ssilvb_gather_batch call must share."""
+    return (req.params.sector_count, str(pool.items[req.key][1].dtype), math.isinf(req.params.thickness),
+            int(getattr(req.params, "step_mode", 0)))
+
+
 class Server:
     """Continuous batching: batches of arrived requests, several in flight on separate streams."""
 
-    def __init__(self, ctx, pool, arena_bytes=1 << 31, max_inflight=4, max_batch=16, max_queue=256, streams=3):
+    def __init__(self, ctx, pool, arena_bytes=1 << 31, max_inflight=4, max_batch=16, max_queue=256, streams=3,
+                 budget_ms=None, rate=4e11):
         import torch
         self.ctx, self.pool = ctx, pool
         self.arena = OutputArena(arena_bytes, pool.device)
         self.max_inflight, self.max_batch, self.max_queue = max_inflight, max_batch, max_queue
+        self.budget_ms, self.rate = budget_ms, rate
         self.streams = [torch.cuda.Stream() for _ in range(streams)]
 
     def run(self, requests, on_done=None, timeout_s=120.0):
         import torch
-        st = Stats()
+        st = Stats(budget_ms=self.budget_ms)
+        adm = LatencyAdmission(None if self.budget_ms is None else self.budget_ms / 1e3, self.rate,
+                               max_in_system=self.max_queue)
+        budget_s = math.inf if self.budget_ms is None else self.budget_ms / 1e3
         reqs = sorted(requests, key=lambda r: r.arrival)
         pending = collections.deque()
-        inflight = collections.deque()  # (event, [(req, off, nbytes, out0, out1)])
-        base = torch.cuda.Event(enable_timing=True)
-        base.record()
-        base.synchronize()
+        inflight = collections.deque()  # (event, t_launch, samples, [(req, off, nbytes, out0, out1, samples)])
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
         i, si = 0, 0
-        n_inflight = 0  # requests in the batches on the GPU
         last_done = 0.0
         while i < len(reqs) or pending or inflight:
             now = time.perf_counter() - t0
             if now > timeout_s:
                 raise RuntimeError("serving run exceeded its time limit")
             while i < len(reqs) and reqs[i].arrival <= now:
-                if len(pending) + n_inflight < self.max_queue:
-                    pending.append(reqs[i])
+                req = reqs[i]
+                H, W = self.pool.shape(req.key)
+                if adm.admit(now, req.arrival, request_samples(H, W, req.params)):
+                    pending.append(req)
                 else:
                     st.dropped += 1
                 i += 1
-            # completions, in launch order
+            # completions, in launch order, timed when the host first sees them
             while inflight and inflight[0][0].query():
-                ev, items = inflight.popleft()
-                n_inflight -= len(items)
-                t_done = base.elapsed_time(ev) / 1e3
-                last_done = max(last_done, t_done)
-                for req, off, nb_, o0, o1 in items:
-                    st.latencies_ms.append((t_done - req.arrival) * 1e3)
+                ev, t_launch, bsamples, items = inflight.popleft()
+                t_done = time.perf_counter() - t0
+                adm.observe(bsamples, t_done - max(t_launch, last_done))
+                last_done = t_done
+                for req, off, nb_, o0, o1, smp in items:
+                    lat = t_done - req.arrival
+                    st.latencies_ms.append(lat * 1e3)
                     st.served += 1
+                    st.within_budget += lat <= budget_s
+                    adm.done(smp)
                     if on_done is not None:
                         on_done(req, o0, o1)
                     self.arena.release(off, nb_)
             # admit and launch the next batch
             if pending and len(inflight) < self.max_inflight:
-                head_nb = pending[0].params.sector_count
+                head_key = _batch_key(self.pool, pending[0])
                 batch, keep, frames = [], None, []
                 skipped = collections.deque()
                 while pending and len(batch) < self.max_batch:
                     req = pending.popleft()
-                    if req.params.sector_count != head_nb:
+                    if _batch_key(self.pool, req) != head_key:
                         skipped.append(req)
                         continue
                     H, W = self.pool.shape(req.key)
@@ -181,18 +253,23 @@ class Server:
                     f, keep = self.ctx.frame(d, n, r, cam, req.params, o0, o1, None, noise=req.noise, sh=req.sh,
                                              keep=keep)
                     frames.append(f)
-                    batch.append((req, off, nb_, o0, o1))
-                    st.samples += H * W * 2 * req.params.num_slices * req.params.steps_per_side
+                    batch.append((req, off, nb_, o0, o1, request_samples(H, W, req.params)))
                 while skipped:
                     pending.appendleft(skipped.pop())
                 if batch:
                     s = self.streams[si % len(self.streams)]
                     si += 1
-                    self.ctx.gather_batch(frames, stream=s)
-                    ev = torch.cuda.Event(enable_timing=True)
+                    try:
+                        self.ctx.gather_batch(frames, stream=s)
+                    except Exception:
+                        for _, off, nb_, *_ in batch:  # nothing was enqueued: give the outputs back
+                            self.arena.release(off, nb_)
+                        raise
+                    ev = torch.cuda.Event()
                     ev.record(s)
-                    inflight.append((ev, batch))
-                    n_inflight += len(batch)
+                    bsamples = sum(b[5] for b in batch)
+                    inflight.append((ev, time.perf_counter() - t0, bsamples, batch))
+                    st.samples += bsamples
                     st.batches += 1
                     st.max_inflight_seen = max(st.max_inflight_seen, len(inflight))
                     continue
@@ -202,10 +279,12 @@ class Server:
 
 
 class PlainServer:
-    """Naive baseline: one launch and one host synchronisation per request, in arrival order."""
+    """Naive baseline: one launch and one host synchronisation per request, in arrival order, under
+    the same admission rule as Server."""
 
-    def __init__(self, ctx, pool, max_queue=256):
+    def __init__(self, ctx, pool, max_queue=256, budget_ms=None, rate=4e11):
         self.ctx, self.pool, self.max_queue = ctx, pool, max_queue
+        self.budget_ms, self.rate = budget_ms, rate
         self.outs = {}
 
     def _outputs(self, key, prm):
@@ -220,9 +299,13 @@ class PlainServer:
 
     def run(self, requests, on_done=None, timeout_s=120.0):
         import torch
-        st = Stats()
+        st = Stats(budget_ms=self.budget_ms)
+        adm = LatencyAdmission(None if self.budget_ms is None else self.budget_ms / 1e3, self.rate,
+                               max_in_system=self.max_queue)
+        budget_s = math.inf if self.budget_ms is None else self.budget_ms / 1e3
         reqs = sorted(requests, key=lambda r: r.arrival)
         stream = torch.cuda.Stream()
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
         last_done = 0.0
         waiting = collections.deque()
@@ -232,8 +315,10 @@ class PlainServer:
             if now > timeout_s:
                 raise RuntimeError("serving run exceeded its time limit")
             while i < len(reqs) and reqs[i].arrival <= now:
-                if len(waiting) < self.max_queue:
-                    waiting.append(reqs[i])
+                req = reqs[i]
+                H, W = self.pool.shape(req.key)
+                if adm.admit(now, req.arrival, request_samples(H, W, req.params)):
+                    waiting.append(req)
                 else:
                     st.dropped += 1
                 i += 1
@@ -243,14 +328,20 @@ class PlainServer:
             req = waiting.popleft()
             d, n, r, cam = self.pool.items[req.key]
             o0, o1 = self._outputs(req.key, req.params)
+            t_start = time.perf_counter() - t0
             self.ctx.gather(d, n, r, cam, req.params, o0, o1, None, noise=req.noise, sh=req.sh, stream=stream)
             stream.synchronize()
             t_done = time.perf_counter() - t0
-            last_done = t_done
-            st.latencies_ms.append((t_done - req.arrival) * 1e3)
-            st.served += 1
             H, W = self.pool.shape(req.key)
-            st.samples += H * W * 2 * req.params.num_slices * req.params.steps_per_side
+            smp = request_samples(H, W, req.params)
+            adm.observe(smp, t_done - max(t_start, last_done))
+            adm.done(smp)
+            last_done = t_done
+            lat = t_done - req.arrival
+            st.latencies_ms.append(lat * 1e3)
+            st.served += 1
+            st.within_budget += lat <= budget_s
+            st.samples += smp
             if on_done is not None:
                 on_done(req, o0, o1)
         st.wall_s = max(last_done, 1e-9) - (reqs[0].arrival if reqs else 0.0)

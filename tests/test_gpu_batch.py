@@ -1,5 +1,6 @@
 """GPU: the batched persistent launch over uneven frames equals per-frame gathers bit for bit,
-and the autotuner's choices change no result."""
+and the autotuner's choices change no result; each batched frame also passes the oracle's parity
+gates on its own (masks against the binary32 replica, outputs against FP64)."""
 import math
 
 import numpy as np
@@ -7,7 +8,7 @@ import pytest
 
 import scenegen
 from scenegen import Params
-from tests.gpu_util import masks_to_u64, run_gpu
+from tests.gpu_util import check_tensors, masks_to_u64, run_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -51,10 +52,12 @@ def _frames(ctx, specs, f16=False):
     return frames, keep, outs, gbs, prms
 
 
-def _check_against_single(ctx, outs, gbs, prms):
+def _check_against_single(ctx, outs, gbs, prms, oracle_check=True):
     noise = scenegen.ign_table()
     sh = scenegen.sh_environment(7)
-    for (o0, o1, m, *_), g, prm in zip(outs, gbs, prms):
+    for k, ((o0, o1, m, *_), g, prm) in enumerate(zip(outs, gbs, prms)):
+        if oracle_check:  # the batched outputs against the oracle, before the single-frame comparison
+            check_tensors(g, prm, noise, sh if prm.ambient_cones else None, o0, o1, m, seed=k)
         ref = run_gpu(ctx, g, prm, noise, sh if prm.ambient_cones else None)
         got0 = o0.cpu().numpy().reshape(-1, 4).astype(np.float64)
         assert np.array_equal(got0, ref[0])

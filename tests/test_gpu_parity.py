@@ -171,6 +171,21 @@ def test_4k_precision_form_sampled(ctx, nb):
     assert info["agree"] > 0.98
 
 
+@pytest.mark.parametrize("nb", [32, 64])
+def test_4k_full_frame_masks_and_outputs_against_the_replica(ctx, nb):
+    """The benchmark workload in full: every one of the 8.29 M x 4 slice masks bit-exact against the
+    binary32 replica, and every pixel's outputs within 1e-6 of it (the same operation sequence).
+    The sampled test above pins those outputs to FP64."""
+    w = scenegen.workload_4k(sector_count=nb)
+    res = run_gpu(ctx, w.gbuf, w.params, w.noise, w.sh)
+    prob = oracle.Problem(w.gbuf, w.params, w.noise, w.sh)
+    r0, r1, rm = oracle.fp32(prob)
+    bad = np.argwhere(res[2] != rm)
+    assert bad.size == 0, f"{len(bad)} of {rm.size} masks differ, first at pixel index {bad[0][0]}"
+    assert np.abs(res[0] - r0).max() <= 1e-6
+    assert np.abs(res[1] - r1).max() <= 1e-6
+
+
 def test_maximum_frame_sampled(ctx):
     """The largest frame the ABI accepts, 16384 x 16384 (2^28 pixels: the largest grid, pixel
     coordinates and mask offsets), FP16 normal/radiance, ambient cones and the masks of every
@@ -347,3 +362,50 @@ def test_temporal_noise_frames(ctx, frame):
     noise = scenegen.ign_table(frame)
     res = run_gpu(ctx, g, prm, noise)
     check_parity(g, prm, noise, None, res)
+
+
+@pytest.mark.parametrize("frame", [0, 5, 63, 64, 200])
+def test_builtin_noise_table_equals_the_ign_input(ctx, frame):
+    """noise_mode 1: the library's own 4x4 interleaved-gradient table (Section 3.1 "directions with
+    random offset"; Section 4.3 temporal jitter) gives the same bits as passing the same table
+    (computed independently on the host) as noise_mode 2, and passes the parity gates."""
+    g = scenegen.render(40 + frame % 7, 72, 56, 10, 3)
+    prm = Params(num_slices=2, steps_per_side=10, sector_count=64, step_mode=frame % 2)
+    a = run_gpu(ctx, g, prm, ("ign", frame))
+    table = scenegen.ign_table(frame)
+    b = run_gpu(ctx, g, prm, table)
+    for x, y in zip(a, b):
+        if x is not None:
+            assert np.array_equal(x, y)
+    check_parity(g, prm, table, None, a, min_agree=0.95)
+
+
+def test_noise_mode_arguments_checked(ctx):
+    import ctypes
+
+    import torch
+
+    import paper_2301_11376_gb300 as ssilvb
+    g = scenegen.render(21, 32, 32, 4, 1)
+    d = torch.from_numpy(g.depth).cuda()
+    n = torch.from_numpy(g.normal).cuda()
+    r = torch.from_numpy(g.radiance).cuda()
+    out0 = torch.full((32, 32, 4), 5.0, device="cuda")
+    with pytest.raises(ssilvb.SsilvbError) as ei:
+        ctx.gather(d, n, r, g.camera, Params(), out0, None, None, noise=("ign", -1))
+    assert ei.value.code == 1
+    keep = ssilvb._HostArrays()
+    table = scenegen.ign_table()
+    gb = ssilvb.Gbuffer(32, 32, d.data_ptr(), 128, n.data_ptr(), 512, 0, r.data_ptr(), 512, 0, None, 0)
+    o = ssilvb.Output(out0.data_ptr(), 512, None, 0, None, None, 0)
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for mode, with_table in [(3, False), (-1, False), (2, False), (0, True), (1, True)]:
+        pc = ssilvb._params_c(Params(), keep, table if with_table else None)
+        pc.noise_mode = mode
+        if not with_table:
+            pc.noise_table = None
+        rc = ctx.lib.ssilvb_gather(ctx.handle, ctypes.byref(gb), ctypes.byref(ssilvb._camera_c(g.camera)),
+                                   ctypes.byref(pc), ctypes.byref(o), s)
+        assert rc == 1, (mode, with_table)
+    torch.cuda.synchronize()
+    assert torch.all(out0 == 5.0)

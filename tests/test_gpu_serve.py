@@ -1,9 +1,14 @@
 """GPU: the continuous-batching server gives every request the same result as a gather of
-that request alone (bit for bit), while batches overlap on the device."""
+that request alone (bit for bit), while batches overlap on the device, and every served result
+passes the oracle's parity gates (outputs against FP64 on sampled pixels)."""
+import dataclasses
+import math
+
 import numpy as np
 import pytest
 
 import scenegen
+from tests.gpu_util import check_tensors
 
 pytestmark = pytest.mark.gpu
 
@@ -17,12 +22,20 @@ def test_serving_results_equal_alone():
     ctx = ssilvb.Context(0)
     pool = serve.ResidentPool()
     sizes = [(160, 90), (320, 180), (256, 144), (480, 270)]
-    keys = []
+    keys, host = [], {}
     for i, (W, H) in enumerate(sizes):
-        pool.add(("s", i), scenegen.render(700 + i, W, H, 16, 4))
+        g = scenegen.render(700 + i, W, H, 16, 4)
+        pool.add(("s", i), g)
         keys.append(("s", i))
+        host[("s", i)] = g
     reqs = serve.poisson_requests(42, 64, 2e-5, keys, None, nd_range=(1, 8), nb_choices=(32, 64),
                                   ns_choices=(8, 16))
+    # mixed kinds in one stream: batches group requests by what a batch call must share
+    for q in reqs:
+        if q.rid % 5 == 1:
+            q.params = dataclasses.replace(q.params, thickness=math.inf)
+        if q.rid % 7 == 2:
+            q.params = dataclasses.replace(q.params, step_mode=1)
     got = {}
 
     def keep(req, o0, o1):
@@ -33,6 +46,7 @@ def test_serving_results_equal_alone():
     torch.cuda.synchronize()
     assert st.served == len(reqs) and st.dropped == 0
     assert st.max_inflight_seen >= 2  # batches overlapped on the device
+    assert srv.arena.free == [(0, srv.arena.size)]  # every output block came back
     for req in reqs:
         d, n, r, cam = pool.items[req.key]
         H, W = d.shape
@@ -40,6 +54,9 @@ def test_serving_results_equal_alone():
         ctx.gather(d, n, r, cam, req.params, o0, None, None, noise=req.noise)
         torch.cuda.synchronize()
         assert torch.equal(got[req.rid], o0), req.rid
+        # the served result against the oracle (no masks in serving: outputs only)
+        check_tensors(host[req.key], req.params, req.noise, None, got[req.rid], n_sample=3000, seed=req.rid,
+                      min_clear=0.5)  # up to 8 slices: fewer pixels clear in every slice
     # the naive baseline serves the same results
     got_plain = {}
     plain = serve.PlainServer(ctx, pool)
@@ -47,6 +64,40 @@ def test_serving_results_equal_alone():
     assert st2.served == 16
     for rid, v in got_plain.items():
         assert torch.equal(v, got[rid])
+    ctx.close()
+
+
+def test_latency_budget_sheds_and_serves_the_rest_correctly():
+    """Under a stream far above capacity with a latency budget, the server sheds at arrival and
+    every request it serves still equals the same request alone."""
+    import torch
+
+    import paper_2301_11376_gb300 as ssilvb
+    from paper_2301_11376_gb300 import serve
+    ssilvb.build()
+    ctx = ssilvb.Context(0)
+    pool = serve.ResidentPool()
+    keys = []
+    for i, (W, H) in enumerate([(1280, 720), (1920, 1080)]):
+        pool.add(("b", i), scenegen.render(720 + i, W, H, 16, 4))
+        keys.append(("b", i))
+    reqs = serve.poisson_requests(43, 300, 1e-5, keys, None, nd_range=(4, 8), nb_choices=(32, 64),
+                                  ns_choices=(16, 32))
+    got = {}
+    srv = serve.Server(ctx, pool, arena_bytes=256 << 20, max_inflight=4, max_batch=8, budget_ms=20.0, rate=4e11)
+    st = srv.run(reqs, on_done=lambda req, o0, o1: got.__setitem__(req.rid, o0.clone()))
+    torch.cuda.synchronize()
+    assert st.dropped > 0 and st.served == len(reqs) - st.dropped and st.served > 0
+    assert st.within_budget <= st.served
+    for req in reqs:
+        if req.rid not in got:
+            continue
+        d, n, r, cam = pool.items[req.key]
+        H, W = d.shape
+        o0, _, _ = ssilvb.alloc_outputs(H, W, req.params, "cuda")
+        ctx.gather(d, n, r, cam, req.params, o0, None, None, noise=req.noise)
+        torch.cuda.synchronize()
+        assert torch.equal(got[req.rid], o0), req.rid
     ctx.close()
 
 
