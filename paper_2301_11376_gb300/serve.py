@@ -18,6 +18,10 @@ from a calibration and follows completed work.  A request predicted to miss the 
 shed at arrival and counted.  Without a budget, a flat bound on the requests in the system
 (queued or on the GPU) sheds arrivals beyond it.
 
+Completed requests are handed to ``on_done(req, out0, out1)`` with views of their outputs.
+Work the callback enqueues on the current CUDA stream (a copy, say) is ordered before any later
+launch that reuses that memory; work it enqueues elsewhere must finish before it returns.
+
 ``PlainServer`` is the naive baseline: one request at a time, one ``ssilvb_gather`` launch
 and one host synchronisation per request, under the same admission rule and the same
 host-side completion clock.
@@ -259,6 +263,9 @@ class Server:
                 if batch:
                     s = self.streams[si % len(self.streams)]
                     si += 1
+                    # work that on_done callbacks enqueued on the current stream (reading outputs whose
+                    # arena blocks this batch may now reuse) runs before the batch
+                    s.wait_stream(torch.cuda.current_stream())
                     try:
                         self.ctx.gather_batch(frames, stream=s)
                     except Exception:
@@ -329,6 +336,8 @@ class PlainServer:
             d, n, r, cam = self.pool.items[req.key]
             o0, o1 = self._outputs(req.key, req.params)
             t_start = time.perf_counter() - t0
+            # the previous on_done's work on the current stream may still read these outputs
+            stream.wait_stream(torch.cuda.current_stream())
             self.ctx.gather(d, n, r, cam, req.params, o0, o1, None, noise=req.noise, sh=req.sh, stream=stream)
             stream.synchronize()
             t_done = time.perf_counter() - t0
