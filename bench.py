@@ -29,6 +29,17 @@ import numpy as np  # noqa: E402
 
 import scenegen  # noqa: E402
 
+
+def _jsonable(o):
+    """numpy scalars in the result line as plain numbers."""
+    if isinstance(o, np.integer):
+        return int(o)
+    if isinstance(o, np.floating):
+        return float(o)
+    if isinstance(o, np.bool_):
+        return bool(o)
+    raise TypeError(f"not JSON serializable: {type(o).__name__}")
+
 SM_COUNT_GB300 = 152
 FP32_LANES_PER_SM = 128
 
@@ -290,7 +301,7 @@ def run_reference(args, world, rank):
                             "sample": f"FP64 oracle, {cores} threads, {n} random pixels per step of the {W}x{H} frame",
                             "cpu_model": cpu_model()},
            "e2e": {"value": value, "unit": "Gsamples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(out))
+    print(json.dumps(out, default=_jsonable))
 
 
 def batch_workload(n_frames=64, base_seed=1000):
@@ -406,7 +417,7 @@ def run_batch_bench(args, world, rank, local):
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": res["workload"], "l2": res["l2"]}, "batch": res, "clocks": clk,
            "gpu_launches": args.steps}
-    print(json.dumps(out))
+    print(json.dumps(out, default=_jsonable))
 
 
 def run_trend_sweep(args, world, rank, local):
@@ -467,7 +478,7 @@ def run_trend_sweep(args, world, rank, local):
            "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
            "config": {"workload": "1920x1080 seed 2, 64 spheres + 16 panels, fp32, N_d 1 with 4x4 IGN rotation",
                       "l2": "flushed between timed runs"}, "rows": rows}
-    print(json.dumps(out))
+    print(json.dumps(out, default=_jsonable))
 
 
 def run_precision_study(args, world, rank, local):
@@ -538,7 +549,7 @@ def serve_pool(dev, rank=0):
     return pool, keys
 
 
-def serve_measure(ctx, pool, keys, seconds, rate_sps, budget_ms=50.0, rank=0):
+def serve_measure(ctx, pool, keys, seconds, rate_sps, budget_ms=50.0, batch_ms=4.0, rank=0):
     """The Poisson serving stream (mean 2000 req/s; 720p-4K, N_d 1-8, N_b 32/64, N_s 8/16/32) and the
     same recipe below capacity (300 req/s), each through the continuous-batching server and through
     the plain per-frame launch with a host synchronisation per request, both under the same
@@ -549,18 +560,20 @@ def serve_measure(ctx, pool, keys, seconds, rate_sps, budget_ms=50.0, rank=0):
     serve.PlainServer(ctx, pool).run(warm[:8])
     out = {"workload": "Poisson arrivals, frames 1280x720..3840x2160 (2 resident scenes per size), N_d 1-8, "
                        "N_b 32/64, N_s 8/16/32, fp32, R 2 m, t 0.5 m, 4x4 IGN noise",
-           "budget_ms": budget_ms, "admission": "shed at arrival when the predicted FIFO latency exceeds the "
-                                                "budget (serve.LatencyAdmission)",
+           "budget_ms": budget_ms, "batch_span_ms": batch_ms,
+           "admission": "shed at arrival when the predicted FIFO latency (plus the batch span for the batching "
+                        "server) exceeds the budget (serve.LatencyAdmission)",
            "clock": "host time when the completion is first observed, both servers",
            "accuracy": "every served result bit-identical to the same request alone, outputs within 1e-4 of FP64 "
                        "(tests/test_gpu_serve.py)"}
     for label, rps, seed in (("load_2000_req_per_s", 2000.0, 77), ("load_300_req_per_s", 300.0, 91)):
         reqs = serve.poisson_requests(seed + rank, int(seconds * rps), 1.0 / rps, keys, None)
         a = serve.Server(ctx, pool, arena_bytes=4 << 30, max_inflight=4, max_batch=16, budget_ms=budget_ms,
-                         rate=rate_sps).run(reqs).summary()
+                         rate=rate_sps, batch_ms=batch_ms).run(reqs).summary()
         b = serve.PlainServer(ctx, pool, budget_ms=budget_ms, rate=rate_sps).run(reqs).summary()
         out[label] = {"requests": len(reqs), "server": a, "plain_per_frame_launch": b,
                       "goodput_ratio": a["goodput_frames_per_s"] / max(b["goodput_frames_per_s"], 1e-9),
+                      "goodput_samples_ratio": a["goodput_gsamples_per_s"] / max(b["goodput_gsamples_per_s"], 1e-9),
                       "frames_per_s_ratio": a["frames_per_s"] / max(b["frames_per_s"], 1e-9)}
     return out
 
@@ -588,7 +601,7 @@ def run_serve_bench(args, world, rank, local):
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": res["workload"], "budget_ms": res["budget_ms"]}, "serve": res, "clocks": clk,
            "gpu_launches": res["load_2000_req_per_s"]["server"]["batches"]}
-    print(json.dumps(out))
+    print(json.dumps(out, default=_jsonable))
 
 # Issue-rate probe: the denominators of the ALU roofline measured on this GPU (scalar FP32 FMA,
 # packed f32x2 FMA, integer ops), each from 8 independent chains per thread on 8 blocks of 256
@@ -676,7 +689,7 @@ def run_issue_peak(args, world, rank, local):
            "ffma2_instructions": elems / float(t_ffma2) / 1e9, "ffma2_fp32_ops": 2 * elems / float(t_ffma2) / 1e9,
            "int_xor_add_ops": 2 * elems / float(t_int) / 1e9, "clocks": clk}
     out["value"] = out["ffma_fp32_ops"]
-    print(json.dumps(out))
+    print(json.dumps(out, default=_jsonable))
 
 
 def main():
@@ -856,7 +869,7 @@ def main():
     if extras is not None:
         out.update({"sector_counts": extras["sector_counts"], "batch": extras["batch"], "serve": extras["serve"],
                     "extras_clocks": extras["clocks"]})
-    print(json.dumps(out))
+    print(json.dumps(out, default=_jsonable))
 
 
 if __name__ == "__main__":

@@ -53,6 +53,7 @@ class Stats:
     dropped: int = 0        # shed at arrival (predicted to miss the budget, or beyond the bound)
     within_budget: int = 0  # served with latency <= budget (all served when there is no budget)
     budget_ms: float | None = None
+    samples_within_budget: int = 0
     latencies_ms: list = field(default_factory=list)
     wall_s: float = 0.0
     batches: int = 0
@@ -66,6 +67,7 @@ class Stats:
                 "frames_per_s": self.served / self.wall_s if self.wall_s > 0 else 0.0,
                 "goodput_frames_per_s": self.within_budget / self.wall_s if self.wall_s > 0 else 0.0,
                 "gsamples_per_s": self.samples / self.wall_s / 1e9 if self.wall_s > 0 else 0.0,
+                "goodput_gsamples_per_s": self.samples_within_budget / self.wall_s / 1e9 if self.wall_s > 0 else 0.0,
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                 "max_ms": float(lat.max()), "mean_ms": float(lat.mean()), "batches": self.batches,
                 "max_batches_in_flight": self.max_inflight_seen, "wall_s": self.wall_s}
@@ -84,16 +86,18 @@ class LatencyAdmission:
     rate: predicted service rate in samples/s (a calibration); observe() moves it toward the
     rate of completed work (exponential average with weight alpha).
     A request of `samples` that arrived at `arrival` is admitted at time `now` iff
-        (now - arrival) + (backlog + samples) / rate <= budget_s,
-    backlog being the samples of every admitted request not yet complete."""
+        (now - arrival) + (backlog + samples) / rate + granularity_s <= budget_s,
+    backlog being the samples of every admitted request not yet complete, and granularity_s the
+    longest a request can wait for work launched together with it to finish (a batch's span)."""
 
-    def __init__(self, budget_s=None, rate=4e11, alpha=0.2, max_in_system=256):
+    def __init__(self, budget_s=None, rate=4e11, alpha=0.2, max_in_system=256, granularity_s=0.0):
         self.budget_s, self.rate, self.alpha, self.max_in_system = budget_s, float(rate), alpha, max_in_system
+        self.granularity_s = granularity_s
         self.backlog = 0
         self.in_system = 0
 
     def predicted_latency(self, now, arrival, samples):
-        return (now - arrival) + (self.backlog + samples) / self.rate
+        return (now - arrival) + (self.backlog + samples) / self.rate + self.granularity_s
 
     def admit(self, now, arrival, samples):
         ok = self.max_in_system is None or self.in_system < self.max_in_system
@@ -186,19 +190,22 @@ class Server:
     """Continuous batching: batches of arrived requests, several in flight on separate streams."""
 
     def __init__(self, ctx, pool, arena_bytes=1 << 31, max_inflight=4, max_batch=16, max_queue=256, streams=3,
-                 budget_ms=None, rate=4e11):
+                 budget_ms=None, rate=4e11, batch_ms=None):
+        """batch_ms: cap on a batch's predicted GPU time (at least one request per batch); None = no cap.
+        With a budget, a request may also wait for the rest of its batch, so admission adds batch_ms."""
         import torch
         self.ctx, self.pool = ctx, pool
         self.arena = OutputArena(arena_bytes, pool.device)
         self.max_inflight, self.max_batch, self.max_queue = max_inflight, max_batch, max_queue
-        self.budget_ms, self.rate = budget_ms, rate
+        self.budget_ms, self.rate, self.batch_ms = budget_ms, rate, batch_ms
         self.streams = [torch.cuda.Stream() for _ in range(streams)]
 
     def run(self, requests, on_done=None, timeout_s=120.0):
         import torch
         st = Stats(budget_ms=self.budget_ms)
+        span_s = 0.0 if self.batch_ms is None else self.batch_ms / 1e3
         adm = LatencyAdmission(None if self.budget_ms is None else self.budget_ms / 1e3, self.rate,
-                               max_in_system=self.max_queue)
+                               max_in_system=self.max_queue, granularity_s=span_s)
         budget_s = math.inf if self.budget_ms is None else self.budget_ms / 1e3
         reqs = sorted(requests, key=lambda r: r.arrival)
         pending = collections.deque()
@@ -229,7 +236,8 @@ class Server:
                     lat = t_done - req.arrival
                     st.latencies_ms.append(lat * 1e3)
                     st.served += 1
-                    st.within_budget += lat <= budget_s
+                    st.within_budget += int(lat <= budget_s)
+                    st.samples_within_budget += smp if lat <= budget_s else 0
                     adm.done(smp)
                     if on_done is not None:
                         on_done(req, o0, o1)
@@ -239,12 +247,18 @@ class Server:
                 head_key = _batch_key(self.pool, pending[0])
                 batch, keep, frames = [], None, []
                 skipped = collections.deque()
+                cap = math.inf if self.batch_ms is None else adm.rate * self.batch_ms / 1e3
+                work = 0
                 while pending and len(batch) < self.max_batch:
                     req = pending.popleft()
                     if _batch_key(self.pool, req) != head_key:
                         skipped.append(req)
                         continue
                     H, W = self.pool.shape(req.key)
+                    if batch and work + request_samples(H, W, req.params) > cap:
+                        skipped.append(req)  # the batch's span is full: the request leads the next one
+                        break
+                    work += request_samples(H, W, req.params)
                     nbytes = _out_bytes(H, W, req.params)
                     got = self.arena.alloc(nbytes)
                     if got is None:  # wait for memory: keep the request at its place in the queue
@@ -349,7 +363,8 @@ class PlainServer:
             lat = t_done - req.arrival
             st.latencies_ms.append(lat * 1e3)
             st.served += 1
-            st.within_budget += lat <= budget_s
+            st.within_budget += int(lat <= budget_s)
+            st.samples_within_budget += smp if lat <= budget_s else 0
             st.samples += smp
             if on_done is not None:
                 on_done(req, o0, o1)
@@ -367,7 +382,7 @@ def poisson_requests(seed, n, mean_gap_s, keys, sizes_of, nd_range=(1, 8), nb_ch
     out = []
     noise = scenegen.ign_table()
     for k in range(n):
-        t += -mean_gap_s * np.log(max(1.0 - u[6 * k], 1e-12))
+        t += float(-mean_gap_s * np.log(max(1.0 - u[6 * k], 1e-12)))
         key = keys[min(int(u[6 * k + 1] * len(keys)), len(keys) - 1)]
         nd = nd_range[0] + min(int(u[6 * k + 2] * (nd_range[1] - nd_range[0] + 1)), nd_range[1] - nd_range[0])
         nb = nb_choices[min(int(u[6 * k + 3] * len(nb_choices)), len(nb_choices) - 1)]
