@@ -196,7 +196,7 @@ def _time_cpu_program(prob, program, H, W, per_px, threads, target_s, rng):
         idx = rng.choice(H * W, size=min(n, H * W), replace=False)
         xy = np.stack([idx % W, idx // W], 1).astype(np.int32)
         t0 = time.perf_counter()
-        run(xy)
+        res = run(xy)
         dt = time.perf_counter() - t0
         if dt >= 0.25 * target_s or n >= H * W:
             break
@@ -204,13 +204,30 @@ def _time_cpu_program(prob, program, H, W, per_px, threads, target_s, rng):
     return {"program": "FP64 oracle" if program == "fp64" else "binary32 replica", "threads": threads,
             "value": len(idx) * per_px / dt / 1e9, "unit": "Gsamples/s", "pixels": int(len(idx)),
             "samples": int(len(idx) * per_px), "seconds": dt,
-            "ms_per_frame_extrapolated": dt / len(idx) * H * W * 1e3}
+            "ms_per_frame_extrapolated": dt / len(idx) * H * W * 1e3}, idx, res
 
 
-def cpu_baseline(w, target_s=6.0):
+def _accuracy(gpu, idx, res, fp64):
+    """The GPU's outputs on the pixels a timed CPU run evaluated: largest and mean absolute
+    difference over AO, GI and ambient, and the share of pixels whose largest difference exceeds
+    1e-4 (against the free-running FP64 oracle, decisions within rounding of a boundary may move a
+    sector between samples; the tests gate every pixel against FP64 on the binary32 decisions)."""
+    g0, g1 = gpu
+    d = np.abs(g0[idx].astype(np.float64) - res[0])
+    if g1 is not None:
+        d = np.concatenate([d[:, :4], np.abs(g1[idx].astype(np.float64) - res[1])[:, :3]], axis=1)
+    worst = d.max(axis=1)
+    return {"against": "FP64 oracle (free-running)" if fp64 else "binary32 replica", "pixels": int(len(idx)),
+            "max_abs": float(worst.max()), "mean_abs": float(d.mean()),
+            "share_above_1e-4": float((worst > 1e-4).mean())}
+
+
+def cpu_baseline(w, target_s=6.0, gpu=None):
     """Both CPU programs of the oracle, as they stand, on the host cores: the FP64 oracle and the
     binary32 replica, each on 1 thread and on every core (OpenMP over pixels), on bounded uniform
-    pixel samples of the workload.  value = the FP64 oracle on every core."""
+    pixel samples of the workload.  value = the FP64 oracle on every core.  gpu: optional host
+    copies (out0, out1) of the GPU's outputs for the same workload, compared with the all-core
+    runs' outputs on their pixels."""
     import oracle
     H, W = w.gbuf.depth.shape
     prob = oracle.Problem(w.gbuf, w.params, w.noise, w.sh)
@@ -218,18 +235,24 @@ def cpu_baseline(w, target_s=6.0):
     cores = os.cpu_count() or 1
     default_threads = oracle.threads()
     rng = np.random.default_rng(7)
-    runs = []
+    runs, accuracy = [], []
     try:
         for program in ("fp64", "fp32"):
             for threads in sorted({1, cores}):
-                runs.append(_time_cpu_program(prob, program, H, W, per_px, threads, target_s, rng))
+                r, idx, res = _time_cpu_program(prob, program, H, W, per_px, threads, target_s, rng)
+                runs.append(r)
+                if gpu is not None and threads == cores:
+                    accuracy.append(_accuracy(gpu, idx, res, program == "fp64"))
     finally:
         oracle.threads(default_threads)
     head = [r for r in runs if r["program"] == "FP64 oracle" and r["threads"] == cores][0]
-    return {"value": head["value"], "unit": "Gsamples/s", "cores": cores, "kind": "oracle",
-            "sample": f"FP64 oracle on {cores} threads, {head['pixels']} uniformly drawn pixels of the {W}x{H} frame "
-                      f"({head['samples']} samples, {head['seconds']:.1f} s); every run below on its own sample",
-            "cpu_model": cpu_model(), "nproc": cores, "runs": runs}
+    out = {"value": head["value"], "unit": "Gsamples/s", "cores": cores, "kind": "oracle",
+           "sample": f"FP64 oracle on {cores} threads, {head['pixels']} uniformly drawn pixels of the {W}x{H} frame "
+                     f"({head['samples']} samples, {head['seconds']:.1f} s); every run below on its own sample",
+           "cpu_model": cpu_model(), "nproc": cores, "runs": runs}
+    if accuracy:
+        out["gpu_accuracy_on_these_pixels"] = accuracy
+    return out
 
 
 def dist_init():
@@ -759,6 +782,9 @@ def main():
     clk = clocks.stop()
     ctx.synchronize(stream)
     kern_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    gpu_host = None
+    if not args.no_cpu_baseline and rank == 0:  # this workload's outputs, compared on the CPU baseline's pixels
+        gpu_host = (out0.cpu().numpy().reshape(-1, 4), out1.cpu().numpy().reshape(-1, 4) if out1 is not None else None)
     t_dev = sum(kern_ms) / 1e3
     t_max = max_over_ranks(world, t_dev)
     value = world * args.steps * spf / t_max / 1e9
@@ -856,7 +882,7 @@ def main():
     alg_gbs = roof["algorithmic_bytes"] / (ms / 1e3) / 1e9
     roof["hbm_context"] = {"algorithmic_GBps": alg_gbs, "peak_GBps": hbm_peak, "frac": alg_gbs / hbm_peak,
                            "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
-    cpu = None if args.no_cpu_baseline else cpu_baseline(w)
+    cpu = None if args.no_cpu_baseline else cpu_baseline(w, gpu=gpu_host)
     out = {"metric": "Gsamples/s (ms/frame at 4K)", "value": value, "unit": "Gsamples/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",

@@ -64,7 +64,7 @@ def _load():
         P = ctypes.POINTER(_Problem)
         vp = ctypes.c_void_p
         lib.orc64_pixels.argtypes = [P, ctypes.c_int, vp, vp, vp, vp, vp, vp]
-        lib.orc64_pixels_ex.argtypes = [P, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp, vp]
+        lib.orc64_pixels_ex.argtypes = [P, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         lib.orc32_pixels.argtypes = [P, ctypes.c_int, vp, vp, vp, vp, vp]
         lib.orc32_pixels_ex.argtypes = [P, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp]
         lib.orc_threads.argtypes = [ctypes.c_int]
@@ -173,7 +173,8 @@ def fp64(prob: Problem, pixels=None, ratio: bool = False, forced: bool = False):
                 raise ValueError(f"orc32_pixels_ex rejected the problem (code {rc})")
         rc = lib.orc64_pixels_ex(ctypes.byref(prob.c), b - a, sub.ctypes.data, o0[a:b].ctypes.data,
                                  o1[a:b].ctypes.data, m[a:b].ctypes.data, g[a:b].ctypes.data,
-                                 r[a:b].ctypes.data if ratio else None, runs.ctypes.data if forced else None, None)
+                                 r[a:b].ctypes.data if ratio else None, runs.ctypes.data if forced else None, None,
+                                 None)
         if rc != 0:
             raise ValueError(f"orc64_pixels_ex rejected the problem (code {rc})")
     out = (o0, o1, (m[..., 0] if prob.words == 1 else m), g)
@@ -195,6 +196,19 @@ def fp32(prob: Problem, pixels=None, counts: bool = False):
     if counts:
         return o0, o1, m, dict(zip(["pixels", "sky", "slices", "samples", "skipped", "gi_fetches", "ops"], c.tolist()))
     return o0, o1, m
+
+
+def step_offsets(prob: Problem, pixels=None) -> np.ndarray:
+    """The pixel offset (dx, dy) every step reads, as the FP64 oracle (and the GPU) decide it in
+    binary32: int32 [n, N_d, 2 sides, N_s, 2], side -omega first; zero for sky pixels."""
+    xy = _pixels(prob, pixels)
+    n = xy.shape[0]
+    st = np.zeros((n, prob.nd, 2, prob.c.steps_per_side, 2), dtype=np.int32)
+    rc = _load().orc64_pixels_ex(ctypes.byref(prob.c), n, xy.ctypes.data, None, None, None, None, None, None,
+                                 None, st.ctypes.data)
+    if rc != 0:
+        raise ValueError(f"orc64_pixels_ex rejected the problem (code {rc})")
+    return st
 
 
 def runs32(prob: Problem, pixels=None) -> np.ndarray:
@@ -266,7 +280,7 @@ def endpoint_trace(prob: Problem, pixels):
     rc = lib.orc32_pixels_ex(ctypes.byref(prob.c), n, xy.ctypes.data, None, None, None, None, None, e32.ctypes.data)
     if rc == 0:
         rc = lib.orc64_pixels_ex(ctypes.byref(prob.c), n, xy.ctypes.data, None, None, None, None, None, None,
-                                 e64.ctypes.data)
+                                 e64.ctypes.data, None)
     if rc != 0:
         raise ValueError(f"oracle rejected the problem (code {rc})")
     return e32, e64

@@ -61,9 +61,12 @@ int orc64_pixels(const orc_problem *pb, int n, const int32_t *xy, double *out0, 
  *     on the binary32 decisions.  margin and ratio still describe the FP64 decisions.  Returns 11
  *     for a run outside [0, N_b].
  *   endpoints (output, 4 doubles): (X_f, X_b, e_f, e_b), the unclamped FP64 sector coordinates and
- *     their binary32 error bounds, written for every visited sample, left as they were elsewhere. */
+ *     their binary32 error bounds, written for every visited sample, left as they were elsewhere.
+ *   steps (output, 2 int32): (dx, dy), the pixel offset each step reads (the binary32 nearest-pixel
+ *     decision), written for every step of a pixel with geometry, on screen or not. */
 int orc64_pixels_ex(const orc_problem *pb, int n, const int32_t *xy, double *out0, double *out1,
-                    uint64_t *masks, double *margin, double *ratio, const int16_t *forced, double *endpoints);
+                    uint64_t *masks, double *margin, double *ratio, const int16_t *forced, double *endpoints,
+                    int32_t *steps);
 
 /* Same, in the binary32 arithmetic of the gather.  counts (may be NULL) receives
  * [0] pixels, [1] sky pixels, [2] slices, [3] samples visited, [4] samples skipped,

@@ -192,9 +192,10 @@ static int validate(const orc_problem *pb) {
  * forced (may be NULL): this pixel's [N_d][2][N_s] block of (lo, hi) sector runs; when given, each
  * sample sets exactly the sectors [lo, hi) instead of those of the FP64 hit rule, and everything
  * else (geometry, cosines, crediting, ambient) stays as below.  ep (may be NULL): this pixel's
- * [N_d][2][N_s] block of (X_f, X_b, e_f, e_b) entries, written for the samples visited. */
+ * [N_d][2][N_s] block of (X_f, X_b, e_f, e_b) entries, written for the samples visited.  steps (may be
+ * NULL): this pixel's [N_d][2][N_s] block of the (dx, dy) pixel offsets every step reads. */
 static void pixel64(const orc_problem *pb, int x, int y, double *o0, double *o1, uint64_t *mk, double *mrg_out,
-                    double *rto_out, const int16_t *forced, double *ep) {
+                    double *rto_out, const int16_t *forced, double *ep, int32_t *steps) {
     const int W = pb->width, H = pb->height, nd = pb->num_slices, ns = pb->steps_per_side;
     const int nb = pb->sector_count, na = pb->ambient_cones;
     const int words = nb == 128 ? 2 : 1;
@@ -278,6 +279,10 @@ static void pixel64(const orc_problem *pb, int x, int y, double *o0, double *o1,
                 }
                 const float dxf = fmaf(off, wsx, 12582912.0f) - 12582912.0f;
                 const float dyf = fmaf(off, wsy, 12582912.0f) - 12582912.0f;
+                if (steps) {
+                    steps[2 * entry] = (int32_t)dxf;
+                    steps[2 * entry + 1] = (int32_t)dyf;
+                }
                 if (dxf == 0.0f && dyf == 0.0f) continue;
                 const int qx = x + (int)dxf, qy = y + (int)dyf;
                 if (qx < 0 || qy < 0 || qx >= W || qy >= H) continue;
@@ -403,7 +408,7 @@ static void pixel64(const orc_problem *pb, int x, int y, double *o0, double *o1,
 }
 
 int orc64_pixels_ex(const orc_problem *pb, int n, const int32_t *xy, double *out0, double *out1, uint64_t *masks,
-                    double *margin, double *ratio, const int16_t *forced, double *endpoints) {
+                    double *margin, double *ratio, const int16_t *forced, double *endpoints, int32_t *steps) {
     int bad = validate(pb);
     if (bad) return bad;
     if (n < 0 || (n > 0 && !xy)) return 10;
@@ -424,13 +429,14 @@ int orc64_pixels_ex(const orc_problem *pb, int n, const int32_t *xy, double *out
         pixel64(pb, xy[2 * pi], xy[2 * pi + 1], out0 ? out0 + 4 * (size_t)pi : NULL,
                 out1 ? out1 + 4 * (size_t)pi : NULL, masks ? masks + (size_t)pi * nd * words : NULL,
                 margin ? margin + (size_t)pi * nd : NULL, ratio ? ratio + (size_t)pi * nd : NULL,
-                forced ? forced + 2 * per_pixel * pi : NULL, endpoints ? endpoints + 4 * per_pixel * pi : NULL);
+                forced ? forced + 2 * per_pixel * pi : NULL, endpoints ? endpoints + 4 * per_pixel * pi : NULL,
+                steps ? steps + 2 * per_pixel * pi : NULL);
     return 0;
 }
 
 int orc64_pixels(const orc_problem *pb, int n, const int32_t *xy, double *out0, double *out1, uint64_t *masks,
                  double *margin, double *ratio) {
-    return orc64_pixels_ex(pb, n, xy, out0, out1, masks, margin, ratio, NULL, NULL);
+    return orc64_pixels_ex(pb, n, xy, out0, out1, masks, margin, ratio, NULL, NULL, NULL);
 }
 
 /* Threads the oracle's pixel loops use: n > 0 sets it; returns the current count (1 without OpenMP). */

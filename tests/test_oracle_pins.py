@@ -718,7 +718,7 @@ def test_forced_empty_runs_give_full_visibility():
     o0 = np.zeros((n, 4)); o1 = np.zeros((n, 4)); m = np.zeros((n, 3), dtype=np.uint64)
     runs = np.zeros((n, 3, 2, 8, 2), dtype=np.int16)
     rc = oracle.lib().orc64_pixels_ex(ctypes.byref(prob.c), n, xy.ctypes.data, o0.ctypes.data, o1.ctypes.data,
-                                      m.ctypes.data, None, None, runs.ctypes.data, None)
+                                      m.ctypes.data, None, None, runs.ctypes.data, None, None)
     assert rc == 0
     assert np.all(m == 0) and np.all(o0[:, 3] == 1.0) and np.all(o0[:, :3] == 0.0)
     geo = np.isfinite(g.depth.reshape(-1)) & (g.depth.reshape(-1) > 0)
@@ -727,7 +727,7 @@ def test_forced_empty_runs_give_full_visibility():
     bad = runs.copy()
     bad[0, 0, 0, 0] = (3, 200)  # a run beyond N_b is rejected
     assert oracle.lib().orc64_pixels_ex(ctypes.byref(prob.c), n, xy.ctypes.data, None, None, None, None, None,
-                                        bad.ctypes.data, None) == 11
+                                        bad.ctypes.data, None, None) == 11
 
 
 def test_results_do_not_depend_on_the_thread_count():
@@ -748,3 +748,42 @@ def test_results_do_not_depend_on_the_thread_count():
     for x, y in zip(a32[:3] + a64 + af, b32[:3] + b64 + bf):
         assert np.array_equal(x, y)
     assert a32[3] == b32[3] and np.array_equal(ar, br)
+
+
+# --- the step offsets against the exact real-number step formula (Algorithm 1, R1, R19) --------
+
+@pytest.mark.parametrize("step_mode,nd,ns,radius", [(0, 4, 32, 2.0), (1, 3, 17, 2.5), (0, 2, 5, 40.0)])
+def test_step_offsets_are_the_nearest_pixels_of_the_exact_offsets(step_mode, nd, ns, radius):
+    """Which pixel step j of side sigma reads is decided in binary32 (the GPU's decision, shared by
+    both CPU programs).  Pinned here against the exact formula, evaluated independently in double
+    precision from the inputs: offset o = (j + 1 + xi_s) r / (N_s + 1) (quadratic steps:
+    r ((j + 1 + xi_s) / (N_s + 1))^2), r = R f_x / z, along sigma (cos phi_i, sin phi_i), phi_i =
+    (i + xi_phi) pi / N_d, image y down in the direction table.  Every offset must be the nearest
+    integer of the exact one per axis: within 1/2 pixel plus a rounding allowance of 1e-5 of the
+    offset.  Using j instead of j + 1, dropping xi_s or flipping a side moves offsets by at least a
+    step (tens of pixels here) and fails."""
+    w = scenegen.workload_4k()
+    prm = Params(nd, ns, radius, 0.5, step_mode=step_mode)
+    prob = oracle.Problem(w.gbuf, prm, w.noise, None)
+    H, W = w.gbuf.depth.shape
+    rng = np.random.default_rng(21 + step_mode)
+    xy = np.stack([rng.integers(0, W, 3000), rng.integers(0, H, 3000)], 1).astype(np.int32)
+    st = oracle.step_offsets(prob, xy).astype(np.float64)          # [n, nd, 2, ns, 2]
+    z = w.gbuf.depth[xy[:, 1], xy[:, 0]].astype(np.float64)
+    geo = np.isfinite(z) & (z > 0)
+    cls = (xy[:, 1] & 3) * 4 + (xy[:, 0] & 3)
+    xi_phi = w.noise[cls, 0].astype(np.float64)
+    xi_s = w.noise[cls, 1].astype(np.float64)
+    r = np.minimum(np.float64(np.float32(radius)) * np.float64(w.gbuf.camera.fx) / np.where(geo, z, 1.0), 2.0 ** 20)
+    j = np.arange(ns, dtype=np.float64)
+    u = (j[None, :] + 1.0 + xi_s[:, None]) / (ns + 1)               # [n, ns]
+    o = r[:, None] * (u * u if step_mode else u)
+    phi = (np.arange(nd)[None, :] + xi_phi[:, None]) * math.pi / nd  # [n, nd]
+    sigma = np.array([-1.0, 1.0])
+    ex = sigma[None, None, :, None] * o[:, None, None, :] * np.cos(phi)[:, :, None, None]
+    ey = sigma[None, None, :, None] * o[:, None, None, :] * np.sin(phi)[:, :, None, None]
+    tol = 0.5 + 1e-5 * np.abs(o)[:, None, None, :] + 1e-6
+    dx, dy = np.abs(st[..., 0] - ex), np.abs(st[..., 1] - ey)
+    assert np.all(dx[geo] <= tol[geo]), dx[geo].max()
+    assert np.all(dy[geo] <= tol[geo]), dy[geo].max()
+    assert np.abs(st[geo]).max() > 50  # not vacuous: offsets of many pixels
