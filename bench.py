@@ -54,6 +54,9 @@ def parse():
                     choices=["4k", "1080p", "256", "batch", "serve", "trends", "precision", "issue_peak"])
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--nb", type=int, default=32)
+    ap.add_argument("--radius", type=float, default=None, help="override the workload's radius R (m)")
+    ap.add_argument("--ns", type=int, default=None, help="override the workload's steps per side")
+    ap.add_argument("--nd", type=int, default=None, help="override the workload's slices per pixel")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
@@ -61,12 +64,21 @@ def parse():
     return ap.parse_args()
 
 
-def make_workload(name, nb):
+def make_workload(name, nb, radius=None, ns=None, nd=None):
+    """The named workload, with optional overrides of R, N_s and N_d (profiling the shapes of the
+    paper's Table 1 and 2 on the same scenes); an override is named in the workload string."""
+    import dataclasses
     if name == "4k":
-        return scenegen.workload_4k(sector_count=nb)
-    if name == "1080p":
-        return scenegen.workload_1080p()
-    return scenegen.workload_256()
+        w = scenegen.workload_4k(sector_count=nb)
+    elif name == "1080p":
+        w = scenegen.workload_1080p()
+    else:
+        w = scenegen.workload_256()
+    over = {k: v for k, v in (("radius", radius), ("steps_per_side", ns), ("num_slices", nd)) if v is not None}
+    if over:
+        w = dataclasses.replace(w, params=dataclasses.replace(w.params, **over),
+                                name=w.name + " " + " ".join(f"{k}={v}" for k, v in over.items()))
+    return w
 
 
 KERNEL_SOURCES = ["gather_kernel.cuh", "launch_impl.cuh", "launch_nb32.cu", "launch_nb64.cu", "launch_nb128.cu",
@@ -292,7 +304,7 @@ def run_reference(args, world, rank):
     runs the oracle)."""
     if rank != 0:
         return
-    w = make_workload(args.workload, args.nb)
+    w = make_workload(args.workload, args.nb, args.radius, args.ns, args.nd)
     import oracle
     H, W = w.gbuf.depth.shape
     prob = oracle.Problem(w.gbuf, w.params, w.noise, w.sh)
@@ -742,7 +754,7 @@ def main():
     ssilvb.build()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    w = make_workload(args.workload, args.nb)
+    w = make_workload(args.workload, args.nb, args.radius, args.ns, args.nd)
     H, W = w.gbuf.depth.shape
     spf = samples_per_frame(w)
     g = w.gbuf
@@ -866,7 +878,9 @@ def main():
     peak_ops = SM_COUNT_GB300 * FP32_LANES_PER_SM * 2.070e9
     achieved = ops / (ms / 1e3)
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
-            "frac": achieved / peak_ops, "traffic": measured_traffic(f"{args.workload} nb{args.nb}"),
+            "frac": achieved / peak_ops,
+            "traffic": (measured_traffic(f"{args.workload} nb{args.nb}")
+                        if args.radius is None and args.ns is None and args.nd is None else None),
             "traffic_unit": "bytes per launch (ncu dram read + write)",
             "algorithmic_bytes": int(H * W * (4 + 2 * g.normal.dtype.itemsize * 4 + 16 + (16 if out1 is not None else 0))),
             "kernel": "gather_class_kernel", "ops_per_launch": ops,
