@@ -339,24 +339,24 @@ def run_reference(args, world, rank):
     print(json.dumps(out, default=_jsonable))
 
 
-def batch_workload(n_frames=64, base_seed=1000):
-    """64 seeded frames of uneven sizes (640x360 .. 2560x1440), per-frame N_d 1-4, N_s 8-32,
-    t 0.1-1.0 m; 64 spheres + 16 panels, FP32 storage, N_b 32, R 2 m, 4x4 IGN noise."""
+def batch_workload(n_frames=64, base_seed=1000, sizes=None):
+    """64 seeded frames of uneven sizes (640x360 .. 2560x1440, or `sizes`), per-frame N_d 1-4, N_s
+    8-32, t 0.1-1.0 m; 64 spheres + 16 panels, FP32 storage, N_b 32, R 2 m, 4x4 IGN noise."""
     out = []
-    for seed, W, H, nd, ns, t in scenegen.batch_recipe(n_frames, base_seed):
+    for seed, W, H, nd, ns, t in scenegen.batch_recipe(n_frames, base_seed, sizes):
         g = scenegen.render(seed, W, H, 64, 16)
         out.append((g, scenegen.Params(nd, ns, 2.0, t)))
     return out
 
 
-def batch_measure(ctx, dev, steps, warmup, base_seed=1000, world=1):
+def batch_measure(ctx, dev, steps, warmup, base_seed=1000, world=1, sizes=None):
     """The 64-frame uneven batch (640x360..2560x1440, per-frame N_d 1-4, N_s 8-32, t 0.1-1 m, FP32,
     N_b 32) through ssilvb_gather_batch in its two forms (one persistent kernel over a tile queue
     launched through a CUDA graph; one graph of per-frame kernels) and as the autotuner picks, against
     the plain per-frame launch with and without a host synchronisation per frame.  CUDA events on the
     launching stream, L2 flushed between timed steps."""
     import torch
-    frames_np = batch_workload(64, base_seed)
+    frames_np = batch_workload(64, base_seed, sizes)
     noise = scenegen.ign_table()
     stream = torch.cuda.current_stream(dev)
     frames, keep, hold = [], None, []
@@ -408,7 +408,9 @@ def batch_measure(ctx, dev, steps, warmup, base_seed=1000, world=1):
     res = {name: timed(fn, steps) for name, fn in forms.items()}
     ctx.set_tuning()
     med = {name: statistics.median(v) for name, v in res.items()}
-    out = {"workload": "batch of 64 uneven frames (640x360..2560x1440), N_d 1-4, N_s 8-32, t 0.1-1.0 m, fp32, nb32",
+    sz = scenegen.BATCH_SIZES if sizes is None else sizes
+    out = {"workload": f"batch of 64 uneven frames ({sz[0][0]}x{sz[0][1]}..{sz[-1][0]}x{sz[-1][1]}), N_d 1-4, "
+                       "N_s 8-32, t 0.1-1.0 m, fp32, nb32",
            "samples_per_batch": samples, "steps": steps, "warmup": warmup,
            "l2": "flushed (256 MB write) between timed steps",
            "tuning": {"occupancy": tuned.occupancy, "rows_per_tile": tuned.rows_per_tile,
@@ -869,6 +871,10 @@ def main():
                 "ops_per_frame": ops_nb, "accuracy": "masks bit-exact against the binary32 replica on the whole "
                                                     "frame (N_b 64; tests/test_gpu_parity.py)"}
         extras["batch"] = batch_measure(ctx, dev, min(args.steps, 10), max(3, min(args.warmup, 5)))
+        # outside the workload configs, for the regime: frames too small to fill the GPU, where
+        # per-launch overhead and host round trips dominate and one batch call pays
+        extras["batch"]["small_frames_outside_configs"] = batch_measure(
+            ctx, dev, min(args.steps, 10), max(3, min(args.warmup, 5)), sizes=scenegen.SMALL_BATCH_SIZES)
         pool, keys = serve_pool(dev)
         extras["serve"] = serve_measure(ctx, pool, keys, args.serve_seconds, value * 1e9)
         extras["clocks"] = xclk.stop()

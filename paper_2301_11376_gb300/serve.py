@@ -221,7 +221,9 @@ class Server:
             while i < len(reqs) and reqs[i].arrival <= now:
                 req = reqs[i]
                 H, W = self.pool.shape(req.key)
-                if adm.admit(now, req.arrival, request_samples(H, W, req.params)):
+                # a request whose outputs exceed the whole arena could never be launched: shed it
+                fits = _out_bytes(H, W, req.params) <= self.arena.size
+                if fits and adm.admit(now, req.arrival, request_samples(H, W, req.params)):
                     pending.append(req)
                 else:
                     st.dropped += 1

@@ -200,13 +200,17 @@ BATCH_SIZES = [(640, 360), (1280, 720), (1920, 1080), (2560, 1440)]
 SERVE_SIZES = [(1280, 720), (1920, 1080), (2560, 1440), (3840, 2160)]
 
 
-def batch_recipe(n_frames: int = 64, base_seed: int = 1000):
+SMALL_BATCH_SIZES = [(160, 90), (192, 108), (256, 144), (320, 180)]
+
+
+def batch_recipe(n_frames: int = 64, base_seed: int = 1000, sizes=None):
     """Per-frame (seed, W, H, N_d, N_s, t) of the uneven batch: sizes uniform over
-    640x360..2560x1440, N_d in 1..4, N_s in 8..32, t in U[0.1, 1.0] m."""
+    640x360..2560x1440 (or over `sizes`), N_d in 1..4, N_s in 8..32, t in U[0.1, 1.0] m."""
+    sizes = BATCH_SIZES if sizes is None else sizes
     out = []
     for i in range(n_frames):
         u = uniform(base_seed + i + 0x5EED, 4)
-        w, h = BATCH_SIZES[min(int(u[0] * 4), 3)]
+        w, h = sizes[min(int(u[0] * len(sizes)), len(sizes) - 1)]
         nd = 1 + min(int(u[1] * 4), 3)
         ns = 8 + min(int(u[2] * 25), 24)
         t = 0.1 + 0.9 * float(u[3])
