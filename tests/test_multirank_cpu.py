@@ -73,6 +73,9 @@ def test_reference_arm_prints_the_contract_line():
     assert d["value"] > 0 and d["unit"] == "Gsamples/s" and d["higher_is_better"] is True
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["sampled"]["pixels_per_step"] < d["sampled"]["pixels_per_frame"]  # extrapolated, and says so
+    assert d["sampled"]["ms_per_frame_extrapolated"] > d["ms_per_step"]  # ms_per_step is the measured step
+    import bench
+    assert d["config"] == bench.line_config(bench.make_workload("4k", 32), 1)  # the main arm's config
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert "3840x2160" in d["config"]["workload"]
