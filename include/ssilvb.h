@@ -277,6 +277,11 @@ ssilvb_status ssilvb_set_tuning(ssilvb_ctx *ctx, const ssilvb_tuning *tuning);
  * the host before a launch), so those two codes are reserved and never returned. */
 ssilvb_status ssilvb_synchronize(ssilvb_ctx *ctx, struct CUstream_st *stream);
 
+/* The same call under the name of the status query in the gather's interface description: waits
+ * for stream (and the asynchronous host-buffer frames) and reports their status, exactly as
+ * ssilvb_synchronize. */
+ssilvb_status ssilvb_get_status(ssilvb_ctx *ctx, struct CUstream_st *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -138,6 +138,8 @@ def load():
         f.restype = ctypes.c_int
     lib.ssilvb_synchronize.argtypes = [vp, vp]
     lib.ssilvb_synchronize.restype = ctypes.c_int
+    lib.ssilvb_get_status.argtypes = [vp, vp]
+    lib.ssilvb_get_status.restype = ctypes.c_int
     lib.ssilvb_set_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
     lib.ssilvb_set_tuning.restype = ctypes.c_int
     lib.ssilvb_gather_batch.argtypes = [vp, ctypes.POINTER(Frame), ctypes.c_int, vp]

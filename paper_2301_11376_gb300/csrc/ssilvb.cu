@@ -409,4 +409,6 @@ ssilvb_status ssilvb_synchronize(ssilvb_ctx *ctx, struct CUstream_st *stream) {
     return SSILVB_OK;
 }
 
+ssilvb_status ssilvb_get_status(ssilvb_ctx *ctx, struct CUstream_st *stream) { return ssilvb_synchronize(ctx, stream); }
+
 }  // extern "C"

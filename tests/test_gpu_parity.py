@@ -147,6 +147,8 @@ def test_deterministic_and_stream(ctx):
     a = run_gpu(ctx, g, prm, noise, stream=s)
     b = run_gpu(ctx, g, prm, noise)
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[2], b[2])
+    import ctypes
+    assert ctx.lib.ssilvb_get_status(ctx.handle, ctypes.c_void_p(s.cuda_stream)) == 0
 
 
 def test_1080p_full_masks_and_sampled_fp64(ctx):
