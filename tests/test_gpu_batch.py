@@ -148,3 +148,31 @@ def test_autotune_keeps_results(ctx):
     t1 = ctx.autotune(one)
     assert t1.mapping in (1, 2)
     _check_against_single(ctx, outs1, gbs1, prms1)
+
+
+def test_batch_builtin_noise_equals_the_table(ctx):
+    """Frames of one batch with the library's built-in noise (noise_mode 1) at different frame
+    indices give the bits of single-frame gathers passed the same tables (noise_mode 2), and
+    pass the oracle's gates."""
+    import torch
+
+    import paper_2301_11376_gb300 as ssilvb
+    specs = [(130 + k, 72 + 16 * k, 40 + 8 * k, dict(num_slices=1 + k % 3, steps_per_side=6 + 3 * k)) for k in range(4)]
+    frames, keep, hold = [], None, []
+    for k, (seed, W, H, kw) in enumerate(specs):
+        g = scenegen.render(seed, W, H, 12, 4)
+        prm = Params(**kw)
+        d = torch.from_numpy(g.depth).cuda()
+        n = torch.from_numpy(g.normal).cuda()
+        r = torch.from_numpy(g.radiance).cuda()
+        o0, o1, m = ssilvb.alloc_outputs(H, W, prm, "cuda", masks=True)
+        f, keep = ctx.frame(d, n, r, g.camera, prm, o0, o1, m, noise=("ign", 3 * k + 1), keep=keep)
+        frames.append(f)
+        hold.append((g, prm, o0, m, scenegen.ign_table(3 * k + 1)))
+    ctx.gather_batch(frames)
+    torch.cuda.synchronize()
+    for g, prm, o0, m, table in hold:
+        ref = run_gpu(ctx, g, prm, table)
+        assert np.array_equal(o0.cpu().numpy().reshape(-1, 4).astype(np.float64), ref[0])
+        assert np.array_equal(masks_to_u64(m, prm.sector_count), ref[2])
+        check_tensors(g, prm, table, None, o0, None, m)
