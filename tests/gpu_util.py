@@ -68,7 +68,8 @@ def pick(a, idx):
     return None if a is None else a[idx]
 
 
-def check_parity(g, prm, noise, sh, gpu, pixels=None, min_agree=0.98, gathered=False, min_clear=None):
+def check_parity(g, prm, noise, sh, gpu, pixels=None, min_agree=0.98, gathered=False, min_clear=None,
+                 mean_gate=True):
     """Compare GPU results with the oracle on `pixels` (all if None).  `gpu` holds full-frame
     arrays, or with gathered=True one row per entry of `pixels`, in that order; its masks may be
     None for a call that wrote no masks (G1 then checks nothing)."""
@@ -122,9 +123,10 @@ def check_parity(g, prm, noise, sh, gpu, pixels=None, min_agree=0.98, gathered=F
     # G4: the mean error against the free-running FP64 oracle over every compared pixel
     all0 = np.abs(g0 - e0)
     mean0 = float(all0.mean()) if all0.size else 0.0
-    assert mean0 <= TOL, mean0
-    if prm.ambient_cones > 0:
-        assert float(np.abs(g1 - e1).mean()) <= TOL
+    if mean_gate:
+        assert mean0 <= TOL, mean0
+        if prm.ambient_cones > 0:
+            assert float(np.abs(g1 - e1).mean()) <= TOL
     # GPU vs replica: the same binary32 sequence, so only accumulation-order effects remain
     assert np.abs(g0 - r0).max(initial=0.0) <= 1e-6
     if prm.ambient_cones > 0:

@@ -31,9 +31,11 @@ def test_random_problem(ctx, k):
     g, prm, noise, table, sh = case(k)
     res = run_gpu(ctx, g, prm, noise, sh)
     # The agreement and clear-pixel floors only guard against a vacuous comparison; random slice
-    # counts up to 16 make fully clear pixels rarer, and the floor/ceil rule with infinite thickness
-    # puts every sample in the tangent plane of a flat surface on a rounding boundary (its back
-    # endpoint sits on the hemisphere edge), so those cases flip often; G3 explains every flip and G2
-    # holds on every pixel either way.
+    # counts up to 16 make fully clear pixels rarer.  The floor/ceil rule with infinite thickness puts
+    # every sample in the tangent plane of a flat surface on a rounding boundary (its run ends on the
+    # hemisphere edge, where floor/ceil is discontinuous), so there FP64 and binary32 flip a sector on
+    # a large share of pixels and the mean difference from the free-running FP64 oracle (G4) exceeds
+    # 1e-4; G3 explains every flip and G2 (FP64 on the binary32 decisions) holds on every pixel.
     boundary_heavy = prm.hit_rule == 1 and math.isinf(prm.thickness)
-    check_parity(g, prm, table, sh, res, min_agree=0.3 if boundary_heavy else 0.9, min_clear=0.0)
+    check_parity(g, prm, table, sh, res, min_agree=0.3 if boundary_heavy else 0.9, min_clear=0.0,
+                 mean_gate=not boundary_heavy)
