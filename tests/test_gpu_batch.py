@@ -168,10 +168,10 @@ def test_batch_builtin_noise_equals_the_table(ctx):
         o0, o1, m = ssilvb.alloc_outputs(H, W, prm, "cuda", masks=True)
         f, keep = ctx.frame(d, n, r, g.camera, prm, o0, o1, m, noise=("ign", 3 * k + 1), keep=keep)
         frames.append(f)
-        hold.append((g, prm, o0, m, scenegen.ign_table(3 * k + 1)))
+        hold.append((g, prm, o0, m, scenegen.ign_table(3 * k + 1), (d, n, r)))  # inputs stay alive
     ctx.gather_batch(frames)
     torch.cuda.synchronize()
-    for g, prm, o0, m, table in hold:
+    for g, prm, o0, m, table, _ in hold:
         ref = run_gpu(ctx, g, prm, table)
         assert np.array_equal(o0.cpu().numpy().reshape(-1, 4).astype(np.float64), ref[0])
         assert np.array_equal(masks_to_u64(m, prm.sector_count), ref[2])
