@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ssilvb", choices=["ssilvb", "reference"])
     ap.add_argument("--workload", default="4k",
-                    choices=["4k", "1080p", "256", "batch", "serve", "trends", "precision", "issue_peak"])
+                    choices=["4k", "1080p", "256", "batch", "serve", "trends", "issue_peak"])
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--nb", type=int, default=32)
     ap.add_argument("--radius", type=float, default=None, help="override the workload's radius R (m)")
@@ -161,19 +161,19 @@ class Clocks:
                 "reasons": reasons, "samples": len(sm)}
 
 
-def algorithmic_ops_per_frame(w, n_pix=24576, seed=123):
-    """Algorithmic lane-ops of one frame: the binary32 replica's op count (one per IEEE
-    add/mul/fma/div/sqrt, compare, select, conversion, shift, logic op, popcount) on a
-    uniform random pixel sample, scaled to the frame."""
-    import oracle
-    H, W = w.gbuf.depth.shape
-    rng = np.random.default_rng(seed)
-    idx = rng.choice(H * W, size=min(n_pix, H * W), replace=False)
-    xy = np.stack([idx % W, idx // W], 1).astype(np.int32)
-    prob = oracle.Problem(w.gbuf, w.params, w.noise, w.sh)
-    _, _, _, c = oracle.fp32(prob, xy, counts=True)
-    scale = (H * W) / len(idx)
-    return c["ops"] * scale, {k: v * scale for k, v in c.items()}
+def algorithmic_ops_per_frame(w):
+    """Algorithmic lane-ops of one frame of workload w: the binary32 replica's op count (one per IEEE
+    add/mul/fma/div/sqrt, compare, select, conversion, shift, logic op, popcount) on a uniform pixel
+    sample scaled to the frame, frozen in profiles/opcounts.json by `python -m oracle.freeze_opcounts`
+    (a CPU test keeps it current).  (None, None) for a workload the table does not hold."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "opcounts.json")) as f:
+            rec = json.load(f).get(w.name)
+    except (OSError, ValueError):
+        rec = None
+    if rec is None:
+        return None, None
+    return rec["ops_per_frame"], rec["counts_per_frame"]
 
 
 def cpu_model():
@@ -525,61 +525,6 @@ def run_trend_sweep(args, world, rank, local):
     print(json.dumps(out, default=_jsonable))
 
 
-def run_precision_study(args, world, rank, local):
-    """FP16 storage of normals and radiance (FP32 depth, FP32 arithmetic) at 4K: error per
-    output (1) against the FP64 oracle on the same FP16 inputs (arithmetic error, the gated
-    one) and (2) against the FP64 oracle on the FP32 G-buffer (storage error, reported), on a
-    uniform pixel sample; bitmask agreement with the binary32 replica on the same sample."""
-    import torch
-
-    import oracle
-    import paper_2301_11376_gb300 as ssilvb
-    ssilvb.build()
-    if rank != 0:
-        return
-    dev = torch.device("cuda", local)
-    ctx = ssilvb.Context(local)
-    g32 = scenegen.render(3, 3840, 2160, 64, 16)
-    g16 = g32.as_f16()
-    noise, sh = scenegen.ign_table(), scenegen.sh_environment(7)
-    H, W = g32.depth.shape
-    rng = np.random.default_rng(17)
-    idx = rng.choice(H * W, 12000, replace=False)
-    xy = np.stack([idx % W, idx // W], 1).astype(np.int32)
-    rows = []
-    for nb in (32, 64, 128):
-        prm = scenegen.Params(4, 32, 2.0, 0.5, sector_count=nb, ambient_cones=4)
-        res = {}
-        for name, g in (("f16", g16), ("f32", g32)):
-            d = torch.from_numpy(g.depth).to(dev)
-            n = torch.from_numpy(np.ascontiguousarray(g.normal)).to(dev)
-            r = torch.from_numpy(np.ascontiguousarray(g.radiance)).to(dev)
-            o0, o1, m = ssilvb.alloc_outputs(H, W, prm, dev, masks=True)
-            ctx.gather(d, n, r, g.camera, prm, o0, o1, m, noise=noise, sh=sh)
-            torch.cuda.synchronize()
-            res[name] = (o0.cpu().numpy().reshape(-1, 4)[idx].astype(np.float64),
-                         o1.cpu().numpy().reshape(-1, 4)[idx].astype(np.float64))
-        e16 = oracle.fp64(oracle.Problem(g16, prm, noise, sh), xy)
-        e32 = oracle.fp64(oracle.Problem(g32, prm, noise, sh), xy)
-
-        def stats(a, b):
-            err = np.abs(a - b)
-            return {"max": float(err.max()), "p99": float(np.percentile(err, 99)), "mean": float(err.mean())}
-        g0, g1 = res["f16"]
-        rows.append({"sector_count": nb,
-                     "arithmetic_vs_fp64_same_fp16_inputs": {"AO": stats(g0[:, 3], e16[0][:, 3]),
-                                                             "GI": stats(g0[:, :3], e16[0][:, :3]),
-                                                             "ambient": stats(g1[:, :3], e16[1][:, :3])},
-                     "storage_vs_fp64_on_fp32_gbuffer": {"AO": stats(g0[:, 3], e32[0][:, 3]),
-                                                         "GI": stats(g0[:, :3], e32[0][:, :3]),
-                                                         "ambient": stats(g1[:, :3], e32[1][:, :3])},
-                     "fp32_storage_vs_fp64": {"AO": stats(res["f32"][0][:, 3], e32[0][:, 3]),
-                                              "GI": stats(res["f32"][0][:, :3], e32[0][:, :3])},
-                     "pixels": len(idx)})
-    print(json.dumps({"metric": "precision study (abs error per output)", "workload": "3840x2160 seed 3, "
-                      "N_d 4, N_s 32, 4 cones, FP16 normal+radiance vs FP32", "rows": rows}))
-
-
 def serve_pool(dev, rank=0):
     """Resident G-buffers of the serving stream: 2 seeded scenes per size, 1280x720 .. 3840x2160."""
     from paper_2301_11376_gb300 import serve
@@ -754,9 +699,6 @@ def main():
     if args.workload == "issue_peak":
         run_issue_peak(args, world, rank, local)
         return
-    if args.workload == "precision":
-        run_precision_study(args, world, rank, local)
-        return
     import torch
 
     import paper_2301_11376_gb300 as ssilvb
@@ -874,7 +816,8 @@ def main():
             m = statistics.median(ts)
             extras["sector_counts"][f"nb{nb}"] = {
                 "ms_per_frame": m, "gsamples_per_s": spf / (m / 1e3) / 1e9, "steps": len(ts),
-                "roofline_frac": ops_nb / (m / 1e3) / (SM_COUNT_GB300 * FP32_LANES_PER_SM * 2.070e9),
+                "roofline_frac": (ops_nb / (m / 1e3) / (SM_COUNT_GB300 * FP32_LANES_PER_SM * 2.070e9)
+                                  if ops_nb is not None else None),
                 "ops_per_frame": ops_nb, "accuracy": "masks bit-exact against the binary32 replica on the whole "
                                                     "frame (N_b 64; tests/test_gpu_parity.py)"}
         extras["batch"] = batch_measure(ctx, dev, min(args.steps, 10), max(3, min(args.warmup, 5)))
@@ -889,15 +832,16 @@ def main():
         return
     ops, counts = algorithmic_ops_per_frame(w)
     peak_ops = SM_COUNT_GB300 * FP32_LANES_PER_SM * 2.070e9
-    achieved = ops / (ms / 1e3)
-    roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
-            "frac": achieved / peak_ops,
+    achieved = ops / (ms / 1e3) if ops is not None else None
+    roof = {"bound": "alu", "achieved": achieved / 1e12 if ops is not None else None, "peak": peak_ops / 1e12,
+            "unit": "Tops/s", "frac": achieved / peak_ops if ops is not None else None,
             "traffic": (measured_traffic(f"{args.workload} nb{args.nb}")
                         if args.radius is None and args.ns is None and args.nd is None else None),
             "traffic_unit": "bytes per launch (ncu dram read + write)",
             "algorithmic_bytes": int(H * W * (4 + 2 * g.normal.dtype.itemsize * 4 + 16 + (16 if out1 is not None else 0))),
             "kernel": "gather_class_kernel", "ops_per_launch": ops,
-            "ops_per_sample": ops / spf,
+            "ops_per_sample": ops / spf if ops is not None else None,
+            "ops_source": "profiles/opcounts.json (binary32 replica op count, frozen)",
             "peak_note": "152 SMs x 128 FP32 lanes x 2.070 GHz max SM clock (derived)"}
     peaks = {}
     try:
