@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--radius", type=float, default=None, help="override the workload's radius R (m)")
     ap.add_argument("--ns", type=int, default=None, help="override the workload's steps per side")
     ap.add_argument("--nd", type=int, default=None, help="override the workload's slices per pixel")
+    ap.add_argument("--no-gi", action="store_true", help="override: AO and ambient only (no indirect-light fetches)")
+    ap.add_argument("--planar", action="store_true",
+                    help="FP16 normal and radiance as two F16X4 planes instead of one interleaved F16X8 plane")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
@@ -64,7 +67,7 @@ def parse():
     return ap.parse_args()
 
 
-def make_workload(name, nb, radius=None, ns=None, nd=None):
+def make_workload(name, nb, radius=None, ns=None, nd=None, gi=None):
     """The named workload, with optional overrides of R, N_s and N_d (profiling the shapes of the
     paper's Table 1 and 2 on the same scenes); an override is named in the workload string."""
     import dataclasses
@@ -74,7 +77,8 @@ def make_workload(name, nb, radius=None, ns=None, nd=None):
         w = scenegen.workload_1080p()
     else:
         w = scenegen.workload_256()
-    over = {k: v for k, v in (("radius", radius), ("steps_per_side", ns), ("num_slices", nd)) if v is not None}
+    over = {k: v for k, v in (("radius", radius), ("steps_per_side", ns), ("num_slices", nd), ("gi", gi))
+            if v is not None}
     if over:
         w = dataclasses.replace(w, params=dataclasses.replace(w.params, **over),
                                 name=w.name + " " + " ".join(f"{k}={v}" for k, v in over.items()))
@@ -313,7 +317,7 @@ def run_reference(args, world, rank):
     oracle)."""
     if rank != 0:
         return
-    w = make_workload(args.workload, args.nb, args.radius, args.ns, args.nd)
+    w = make_workload(args.workload, args.nb, args.radius, args.ns, args.nd, False if args.no_gi else None)
     import oracle
     H, W = w.gbuf.depth.shape
     prob = oracle.Problem(w.gbuf, w.params, w.noise, w.sh)
@@ -705,13 +709,18 @@ def main():
     ssilvb.build()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    w = make_workload(args.workload, args.nb, args.radius, args.ns, args.nd)
+    w = make_workload(args.workload, args.nb, args.radius, args.ns, args.nd, False if args.no_gi else None)
     H, W = w.gbuf.depth.shape
     spf = samples_per_frame(w)
     g = w.gbuf
     d = torch.from_numpy(g.depth).to(dev)
-    n = torch.from_numpy(np.ascontiguousarray(g.normal)).to(dev)
-    r = torch.from_numpy(np.ascontiguousarray(g.radiance)).to(dev)
+    # FP16 storage: by default one interleaved plane (F16X8: a sample's normal and radiance in one
+    # 16-byte record, the same bytes per pixel as two F16X4 planes); --planar: the two planes
+    interleaved = g.normal.dtype == np.float16 and not args.planar
+    n_host = g.interleaved_f16() if interleaved else np.ascontiguousarray(g.normal)
+    r_host = None if interleaved else np.ascontiguousarray(g.radiance)
+    n = torch.from_numpy(n_host).to(dev)
+    r = torch.from_numpy(r_host).to(dev) if r_host is not None else None
     out0, out1, _ = ssilvb.alloc_outputs(H, W, w.params, dev)
     ctx = ssilvb.Context(local)
     stream = torch.cuda.current_stream(dev)
@@ -757,7 +766,8 @@ def main():
     e2e = None
     if not args.no_e2e:
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
-        hd, hn, hr = pin(g.depth), pin(g.normal), pin(g.radiance)
+        hd, hn = pin(g.depth), pin(n_host)
+        hr = pin(r_host) if r_host is not None else None
         ho0 = torch.empty((H, W, 4), dtype=torch.float32).pin_memory()
         ho1 = torch.empty((H, W, 4), dtype=torch.float32).pin_memory() if out1 is not None else None
         # a stream of frames through the pipelined host-buffer call (one frame's copies overlap the
@@ -783,7 +793,7 @@ def main():
         for _ in range(ke):
             ctx.gather_host(hd, hn, hr, g.camera, w.params, ho0, ho1, None, noise=w.noise, sh=w.sh, stream=stream)
         ts = max_over_ranks(world, time.perf_counter() - t0)
-        h2d = hd.numel() * 4 + hn.numel() * hn.element_size() + hr.numel() * hr.element_size()
+        h2d = hd.numel() * 4 + hn.numel() * hn.element_size() + (hr.numel() * hr.element_size() if hr is not None else 0)
         d2h = ho0.numel() * 4 + (ho1.numel() * 4 if ho1 is not None else 0)
         e2e = {"value": world * ke * spf / te / 1e9, "unit": "Gsamples/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": te / ke * 1e3,
@@ -820,6 +830,28 @@ def main():
                                   if ops_nb is not None else None),
                 "ops_per_frame": ops_nb, "accuracy": "masks bit-exact against the binary32 replica on the whole "
                                                     "frame (N_b 64; tests/test_gpu_parity.py)"}
+        if g.normal.dtype == np.float16:
+            # the same workload with the other FP16 layout, for comparison (same results bit for bit)
+            other = (torch.from_numpy(np.ascontiguousarray(g.normal)).to(dev),
+                     torch.from_numpy(np.ascontiguousarray(g.radiance)).to(dev)) if interleaved else \
+                (torch.from_numpy(g.interleaved_f16()).to(dev), None)
+            ts = []
+            for i in range(args.warmup + min(args.steps, 10)):
+                flush.fill_(float(i))
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                ctx.gather(d, other[0], other[1], g.camera, w.params, out0, out1, None, noise=w.noise, sh=w.sh,
+                           stream=stream)
+                b.record(stream)
+                torch.cuda.synchronize()
+                if i >= args.warmup:
+                    ts.append(a.elapsed_time(b))
+            del other
+            extras["storage_layouts"] = {
+                "f16x8_interleaved_ms": ms if interleaved else statistics.median(ts),
+                "f16x4_planar_ms": statistics.median(ts) if interleaved else ms,
+                "note": "FP16 normal and radiance as one interleaved plane (a sample's normal and radiance in one "
+                        "16-byte record) or two planes; the same values, bit-identical results"}
         extras["batch"] = batch_measure(ctx, dev, min(args.steps, 10), max(3, min(args.warmup, 5)))
         # outside the workload configs, for the regime: frames too small to fill the GPU, where
         # per-launch overhead and host round trips dominate and one batch call pays
@@ -836,7 +868,8 @@ def main():
     roof = {"bound": "alu", "achieved": achieved / 1e12 if ops is not None else None, "peak": peak_ops / 1e12,
             "unit": "Tops/s", "frac": achieved / peak_ops if ops is not None else None,
             "traffic": (measured_traffic(f"{args.workload} nb{args.nb}")
-                        if args.radius is None and args.ns is None and args.nd is None else None),
+                        if args.radius is None and args.ns is None and args.nd is None and not args.no_gi
+                        and not args.planar else None),
             "traffic_unit": "bytes per launch (ncu dram read + write)",
             "algorithmic_bytes": int(H * W * (4 + 2 * g.normal.dtype.itemsize * 4 + 16 + (16 if out1 is not None else 0))),
             "kernel": "gather_class_kernel", "ops_per_launch": ops,
@@ -858,12 +891,14 @@ def main():
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": line_config(w, world),
+           "layout": ("F16X8 (normal and radiance interleaved)" if interleaved else
+                      "F16X4 planes" if g.normal.dtype == np.float16 else "F32X4 planes"),
            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": args.steps,
            "kernel_ms": {"min": min(kern_ms), "median": statistics.median(kern_ms), "max": max(kern_ms)},
            "wall_s_timed_region": wall}
     if extras is not None:
-        out.update({"sector_counts": extras["sector_counts"], "batch": extras["batch"], "serve": extras["serve"],
-                    "extras_clocks": extras["clocks"]})
+        out.update({k: extras[k] for k in ("sector_counts", "storage_layouts", "batch", "serve") if k in extras})
+        out["extras_clocks"] = extras["clocks"]
     print(json.dumps(out, default=_jsonable))
 
 

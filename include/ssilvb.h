@@ -56,15 +56,20 @@ typedef enum {
     SSILVB_ERR_DEVICE_CHECK = 6   /* a device-side consistency check failed */
 } ssilvb_status;
 
-/* Storage of the normal and radiance planes: 4 components per pixel
- * (xyz / rgb, the 4th ignored), 32-bit float or IEEE binary16. */
-typedef enum { SSILVB_FMT_F32X4 = 0, SSILVB_FMT_F16X4 = 1 } ssilvb_format;
+/* Storage of normals and radiance.  F32X4 / F16X4: two planes, 4 components per pixel (xyz / rgb,
+ * the 4th ignored), 32-bit float or IEEE binary16.  F16X8: one interleaved plane of 8 binary16 per
+ * pixel, (n.x, n.y, n.z, c.r, c.g, c.b, unused, unused), 16 bytes, the footprint of the two F16X4
+ * planes: a sample's normal and radiance then share one 32-byte memory sector, which halves the
+ * sectors the indirect-light fetches read (the values, and so every result, are those of F16X4). */
+typedef enum { SSILVB_FMT_F32X4 = 0, SSILVB_FMT_F16X4 = 1, SSILVB_FMT_F16X8 = 2 } ssilvb_format;
 
 /* The G-buffer the gather reads (Algorithm 1 inputs p, n_p and the light buffer of
  * Section 3.3: depth, view-space normals and direct radiance "with shadows").
  * Device pointers, row-major with a row pitch in BYTES; base pointers 16-byte
  * aligned; depth pitch a multiple of 4, normal/radiance pitch a multiple of the
- * pixel size (16 for F32X4, 8 for F16X4).  normal_fmt must equal radiance_fmt. */
+ * pixel size (16 for F32X4, 8 for F16X4, 16 for F16X8).  normal_fmt must equal radiance_fmt.
+ * F16X8: normal and radiance are the same pointer and pitch (the interleaved plane); the
+ * multi-bounce light buffer (light_out, direct) is not available with it (UNSUPPORTED). */
 typedef struct {
     int width, height;            /* 1 .. 16384 each */
     const float *depth;           /* [height][pitch] linear view depth */

@@ -30,7 +30,7 @@ NVCC_FLAGS = [
 SSILVB_OK = 0
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "OUT_OF_MEMORY", 4: "CUDA", 5: "TIMEOUT",
                 6: "DEVICE_CHECK"}
-FMT_F32X4, FMT_F16X4 = 0, 1
+FMT_F32X4, FMT_F16X4, FMT_F16X8 = 0, 1, 2
 
 
 def _sources():
@@ -221,12 +221,23 @@ def _params_c(p, keep: _HostArrays, noise=None, sh=None) -> ParamsC:
 
 
 def _fmt(t):
+    """Storage format of a normal / radiance tensor: [H, W, 4] float32 or float16 planes, or one
+    [H, W, 8] float16 plane interleaving normal and radiance (F16X8)."""
     import torch
-    if t.dtype == torch.float32:
+    if t.dtype == torch.float32 and t.shape[-1] == 4:
         return FMT_F32X4
     if t.dtype == torch.float16:
-        return FMT_F16X4
-    raise TypeError(f"normal/radiance dtype {t.dtype} not float32/float16")
+        return FMT_F16X8 if t.shape[-1] == 8 else FMT_F16X4
+    raise TypeError(f"normal/radiance dtype {t.dtype} with {t.shape[-1]} components is not a storage format")
+
+
+def _radiance_of(normal, radiance):
+    """The radiance plane: for an interleaved F16X8 normal plane it is that plane itself."""
+    if radiance is None:
+        if _fmt(normal) != FMT_F16X8:
+            raise ValueError("radiance is required unless normal is an interleaved [H, W, 8] float16 plane")
+        return normal
+    return radiance
 
 
 def _pitch(t, last_dims_elems):
@@ -271,6 +282,7 @@ class Context:
         out0 [H,W,4] f32, out1 [H,W,4] f32 (ambient), masks [N_d,H,W] int32|int64 or None."""
         import torch
         H, W = depth.shape
+        radiance = _radiance_of(normal, radiance)
         g = Gbuffer(W, H, depth.data_ptr(), _pitch(depth, 1), normal.data_ptr(), _pitch(normal, 4), _fmt(normal),
                     radiance.data_ptr(), _pitch(radiance, 4), _fmt(radiance),
                     direct.data_ptr() if direct is not None else None, _pitch(direct, 4) if direct is not None else 0)
@@ -299,8 +311,16 @@ class Context:
             st = a.stride(0) * a.element_size() if hasattr(a, "element_size") else a.strides[0]
             return st
 
-        nfmt = FMT_F16X4 if (str(normal.dtype).endswith("float16")) else FMT_F32X4
-        rfmt = FMT_F16X4 if (str(radiance.dtype).endswith("float16")) else FMT_F32X4
+        def hfmt(a):  # numpy arrays or CPU tensors
+            if str(a.dtype).endswith("float16"):
+                return FMT_F16X8 if a.shape[-1] == 8 else FMT_F16X4
+            return FMT_F32X4
+
+        if radiance is None:
+            if hfmt(normal) != FMT_F16X8:
+                raise ValueError("radiance is required unless normal is an interleaved [H, W, 8] float16 plane")
+            radiance = normal
+        nfmt, rfmt = hfmt(normal), hfmt(radiance)
         H, W = depth.shape[:2]
         g = Gbuffer(W, H, ptr(depth), pitch(depth), ptr(normal), pitch(normal), nfmt, ptr(radiance), pitch(radiance),
                     rfmt, ptr(direct) if direct is not None else None, pitch(direct) if direct is not None else 0)
@@ -320,6 +340,7 @@ class Context:
         """An ssilvb_frame for gather_batch from device tensors (host arrays kept alive in `keep`)."""
         H, W = depth.shape
         keep = keep if keep is not None else _HostArrays()
+        radiance = _radiance_of(normal, radiance)
         f = Frame()
         f.gbuffer = Gbuffer(W, H, depth.data_ptr(), _pitch(depth, 1), normal.data_ptr(), _pitch(normal, 4),
                             _fmt(normal), radiance.data_ptr(), _pitch(radiance, 4), _fmt(radiance))

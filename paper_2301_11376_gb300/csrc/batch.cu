@@ -88,7 +88,7 @@ ssilvb_status run_batch(ssilvb_ctx *ctx, const ssilvb_frame *frames, int n, cuda
     if (!frames || n < 1 || n > kMaxFrames)
         return fail(ctx, SSILVB_ERR_INVALID_ARG, "n_frames %d outside 1..%d (or frames NULL)", n, kMaxFrames);
     const int nb = frames[0].params.sector_count;
-    const bool f16 = frames[0].gbuffer.normal_fmt == SSILVB_FMT_F16X4;
+    const bool f16 = half_storage(frames[0].gbuffer.normal_fmt);
     const bool inf_t = std::isinf(frames[0].params.thickness);
     const int sm = frames[0].params.step_mode;
     int max_nd = 0, max_ns = 0;
@@ -100,7 +100,7 @@ ssilvb_status run_batch(ssilvb_ctx *ctx, const ssilvb_frame *frames, int n, cuda
             std::string d = ctx->last_error;
             return fail(ctx, s, "frame %d: %s", i, d.c_str());
         }
-        if (f.params.sector_count != nb || (f.gbuffer.normal_fmt == SSILVB_FMT_F16X4) != f16 ||
+        if (f.params.sector_count != nb || half_storage(f.gbuffer.normal_fmt) != f16 ||
             (bool)std::isinf(f.params.thickness) != inf_t || f.params.step_mode != sm)
             return fail(ctx, SSILVB_ERR_UNSUPPORTED,
                         "frame %d: sector count, storage format, infinite thickness and step mode must match frame 0",
@@ -250,7 +250,7 @@ float time_runs(ssilvb_ctx *ctx, const ssilvb_frame *frames, int n, cudaStream_t
             GatherParams P;
             fill_params(P, &frames[0].gbuffer, &frames[0].camera, &frames[0].params, &frames[0].out);
             cudaError_t e = launch_single(P, frames[0].params.sector_count,
-                                          frames[0].gbuffer.normal_fmt == SSILVB_FMT_F16X4,
+                                          half_storage(frames[0].gbuffer.normal_fmt),
                                           std::isinf(frames[0].params.thickness), k, st);
             s = e == cudaSuccess ? SSILVB_OK : cuda_fail(ctx, e, "autotune launch");
         } else {
@@ -343,7 +343,7 @@ ssilvb_status ssilvb_autotune(ssilvb_ctx *ctx, const ssilvb_frame *frames, int n
     }
     TuneKey kb;
     kb.nb = frames[0].params.sector_count;
-    kb.f16 = frames[0].gbuffer.normal_fmt == SSILVB_FMT_F16X4;
+    kb.f16 = half_storage(frames[0].gbuffer.normal_fmt);
     kb.inf_t = std::isinf(frames[0].params.thickness) ? 1 : 0;
     kb.size_class = (int)std::ceil(std::log2(px > 1.0 ? px : 1.0));
     kb.nd = max_nd;

@@ -56,6 +56,7 @@ struct GatherParams {
     int y0, y1;            // centre-pixel rows [y0, y1) this launch covers (samples read the whole frame)
     int nd, ns, na;
     int hit_rule, step_mode, gi;
+    int nr16;              // normal and radiance interleaved: one 16-byte record per pixel (F16X8)
     // per-launch binary32 constants
     float inv_fx, inv_fy, kx0, ninv_fy, ky0;
     float Rfx, dn, K, half_nb, f_nb, inv_nb, inv_nd;
@@ -254,6 +255,36 @@ __device__ __forceinline__ float3 load_xyz(const char *base, size_t pitch, int x
     }
 }
 
+// A sample's normal and radiance: from the two planes, or (F16X8, binary16 only) from its one
+// 16-byte interleaved record (n.x, n.y, n.z, c.r, c.g, c.b, -, -) in a single load.  The values are
+// the same binary16 numbers either way.
+template <bool F16>
+__device__ __forceinline__ void load_normal_radiance(const GatherParams &P, int x, int y, float3 &n, float3 &c) {
+    if (F16 && P.nr16) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(P.normal + (size_t)y * P.normal_pitch) + x);
+        const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&v.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&v.y));
+        const float2 d = __half22float2(*reinterpret_cast<const __half2 *>(&v.z));
+        n = make_float3(a.x, a.y, b.x);
+        c = make_float3(b.y, d.x, d.y);
+    } else {
+        c = load_xyz<F16>(P.radiance, P.radiance_pitch, x, y);
+        n = load_xyz<F16>(P.normal, P.normal_pitch, x, y);
+    }
+}
+
+// The centre pixel's normal: its plane, or the first half of its interleaved record.
+template <bool F16>
+__device__ __forceinline__ float3 load_normal(const GatherParams &P, int x, int y) {
+    if (F16 && P.nr16) {
+        const uint2 v = __ldg(reinterpret_cast<const uint2 *>(P.normal + (size_t)y * P.normal_pitch) + 2 * x);
+        const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&v.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&v.y));
+        return make_float3(a.x, a.y, b.x);
+    }
+    return load_xyz<F16>(P.normal, P.normal_pitch, x, y);
+}
+
 // 0 < z < +INF (NaN and negative values fail): positive finite binary32 bit patterns are 1 .. 0x7f7fffff.
 __device__ __forceinline__ bool is_geometry(float z) { return __float_as_uint(z) - 1u < 0x7f7fffffu; }
 
@@ -325,8 +356,8 @@ __device__ __forceinline__ void occlude(const GatherParams &P, const Pixel &X, f
     const int newly = popc_(bj & ~b);
     b |= bj;
     if (newly > 0 && P.gi) {
-        const float3 cj = load_xyz<F16>(P.radiance, P.radiance_pitch, qx, qy);
-        const float3 nj = load_xyz<F16>(P.normal, P.normal_pitch, qx, qy);
+        float3 cj, nj;
+        load_normal_radiance<F16>(P, qx, qy, nj, cj);
         const float cp = fmaxf(fmaf(X.n.x, lx, fmaf(X.n.y, ly, X.n.z * lz)) * rl, 0.0f);
         const float cq = fmaxf(-(fmaf(nj.x, lx, fmaf(nj.y, ly, nj.z * lz)) * rl), 0.0f);
         const float wgt = (((float)newly * P.inv_nb) * cp) * cq;
@@ -529,7 +560,7 @@ __device__ __forceinline__ void gather_pixel(const GatherParams &P, int x, int y
     X.vx = -(X.ax * rd);
     X.vy = -(X.by * rd);
     X.vz = rd;
-    X.n = load_xyz<F16>(P.normal, P.normal_pitch, x, y);
+    X.n = load_normal<F16>(P, x, y);
     const float rpx = fminf(P.Rfx / z, 1048576.0f);
     const int cls = (y & 3) * 4 + (x & 3);
     const float xidn = P.xi_s[cls] * P.dn;

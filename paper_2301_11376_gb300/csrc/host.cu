@@ -91,6 +91,8 @@ static ssilvb_status enqueue_frame(ssilvb_ctx *ctx, HostLane &L, const ssilvb_gb
                                    const ssilvb_camera *camera, const ssilvb_params *params,
                                    const ssilvb_output *out) {
     const size_t W = gbuffer->width, H = gbuffer->height;
+    // bytes per pixel of one normal / radiance plane; F16X8 is one plane holding both
+    const bool nr16 = gbuffer->normal_fmt == SSILVB_FMT_F16X8;
     const size_t px = gbuffer->normal_fmt == SSILVB_FMT_F16X4 ? 8 : 16;
     const int na = params->ambient_cones;
     const size_t melem = params->sector_count / 8;
@@ -99,7 +101,8 @@ static ssilvb_status enqueue_frame(ssilvb_ctx *ctx, HostLane &L, const ssilvb_gb
     const size_t b_depth = up(W * H * 4), b_px = up(W * H * px), b_out = up(W * H * 16);
     const size_t b_light = out->light_out ? up(W * H * px) : 0;
     const size_t b_direct = (out->light_out && gbuffer->direct) ? up(W * H * px) : 0;
-    const size_t need = b_depth + 2 * b_px + b_out + (na > 0 ? b_out : 0) + up(mask_bytes) + b_light + b_direct;
+    const size_t need = b_depth + (nr16 ? 1 : 2) * b_px + b_out + (na > 0 ? b_out : 0) + up(mask_bytes) + b_light +
+                        b_direct;
     if (need > L.stage_bytes) {
         if (L.stage) {
             drain_lane(L);
@@ -117,7 +120,7 @@ static ssilvb_status enqueue_frame(ssilvb_ctx *ctx, HostLane &L, const ssilvb_gb
     char *base = static_cast<char *>(L.stage);
     float *d_depth = reinterpret_cast<float *>(base);
     char *d_normal = base + b_depth;
-    char *d_rad = d_normal + b_px;
+    char *d_rad = nr16 ? d_normal : d_normal + b_px;
     char *d_out0 = d_rad + b_px;
     char *d_out1 = na > 0 ? d_out0 + b_out : nullptr;
     char *d_masks = out->masks ? d_out0 + b_out + (na > 0 ? b_out : 0) : nullptr;
@@ -129,7 +132,7 @@ static ssilvb_status enqueue_frame(ssilvb_ctx *ctx, HostLane &L, const ssilvb_gb
     if (e == cudaSuccess)
         e = cudaMemcpy2DAsync(d_normal, W * px, gbuffer->normal, gbuffer->normal_pitch, W * px, H,
                               cudaMemcpyHostToDevice, L.in);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && !nr16)
         e = cudaMemcpy2DAsync(d_rad, W * px, gbuffer->radiance, gbuffer->radiance_pitch, W * px, H,
                               cudaMemcpyHostToDevice, L.in);
     if (e == cudaSuccess && d_direct)
@@ -172,7 +175,7 @@ static ssilvb_status enqueue_frame(ssilvb_ctx *ctx, HostLane &L, const ssilvb_gb
         cudaStream_t ls = L.comp[b & 1];
         P.y0 = (int)y0;
         P.y1 = (int)y1;
-        e = launch_single(P, params->sector_count, gbuffer->normal_fmt == SSILVB_FMT_F16X4,
+        e = launch_single(P, params->sector_count, half_storage(gbuffer->normal_fmt),
                           std::isinf(params->thickness), k, ls);
         if (e == cudaSuccess) e = cudaEventRecord(L.band_done[b], ls);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(L.out, L.band_done[b], 0);

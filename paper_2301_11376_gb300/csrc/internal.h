@@ -39,6 +39,10 @@ struct KernelChoice {
     int batch_mode = 2;              // batch: 1 persistent tile queue, 2 graph of per-frame kernels
 };
 
+// Normal and radiance stored as binary16 (two F16X4 planes or one interleaved F16X8 plane): the
+// kernels' F16 variants.
+inline bool half_storage(int fmt) { return fmt == SSILVB_FMT_F16X4 || fmt == SSILVB_FMT_F16X8; }
+
 // Default register budget of the class and batch kernels (measured at 4K, CUDA events): 8 blocks of
 // 128 threads per SM for N_b = 32 (1 % faster than 9), 9 for N_b = 64 and 128 (1.5 % faster than 8).
 inline int default_minb(int nb) { return nb == 32 ? 8 : 9; }

@@ -70,14 +70,14 @@ extern "C" ssilvb_status ssilvb_gather_batch_noalloc(const ssilvb_frame *frames,
     ssilvb_ctx probe;
     probe.device = dev;
     const int nb = frames[0].params.sector_count;
-    const bool f16 = frames[0].gbuffer.normal_fmt == SSILVB_FMT_F16X4;
+    const bool f16 = half_storage(frames[0].gbuffer.normal_fmt);
     const bool inf_t = std::isinf(frames[0].params.thickness);
     const int sm = frames[0].params.step_mode;
     for (int i = 0; i < n_frames; ++i) {
         const ssilvb_frame &f = frames[i];
         st = validate(&probe, &f.gbuffer, &f.camera, &f.params, &f.out, true);
         if (st != SSILVB_OK) return fail(nullptr, st, "frame %d: %s", i, probe.last_error.c_str());
-        if (f.params.sector_count != nb || (f.gbuffer.normal_fmt == SSILVB_FMT_F16X4) != f16 ||
+        if (f.params.sector_count != nb || half_storage(f.gbuffer.normal_fmt) != f16 ||
             (bool)std::isinf(f.params.thickness) != inf_t || f.params.step_mode != sm)
             return fail(nullptr, SSILVB_ERR_UNSUPPORTED,
                         "frame %d: sector count, storage format, infinite thickness and step mode must match frame 0",

@@ -45,12 +45,18 @@ ssilvb_status validate(ssilvb_ctx *ctx, const ssilvb_gbuffer *g, const ssilvb_ca
     if (g->width < 1 || g->height < 1 || g->width > 16384 || g->height > 16384)
         return fail(ctx, SSILVB_ERR_INVALID_ARG, "image size %dx%d outside 1..16384", g->width, g->height);
     if (!g->depth || !g->normal || !g->radiance) return fail(ctx, SSILVB_ERR_INVALID_ARG, "null G-buffer plane");
-    if (g->normal_fmt != SSILVB_FMT_F32X4 && g->normal_fmt != SSILVB_FMT_F16X4)
+    if (g->normal_fmt != SSILVB_FMT_F32X4 && g->normal_fmt != SSILVB_FMT_F16X4 && g->normal_fmt != SSILVB_FMT_F16X8)
         return fail(ctx, SSILVB_ERR_INVALID_ARG, "unknown normal format %d", g->normal_fmt);
-    if (g->radiance_fmt != SSILVB_FMT_F32X4 && g->radiance_fmt != SSILVB_FMT_F16X4)
+    if (g->radiance_fmt != SSILVB_FMT_F32X4 && g->radiance_fmt != SSILVB_FMT_F16X4 &&
+        g->radiance_fmt != SSILVB_FMT_F16X8)
         return fail(ctx, SSILVB_ERR_INVALID_ARG, "unknown radiance format %d", g->radiance_fmt);
     if (g->normal_fmt != g->radiance_fmt)
         return fail(ctx, SSILVB_ERR_UNSUPPORTED, "normal and radiance formats must match");
+    const bool nr16 = g->normal_fmt == SSILVB_FMT_F16X8;
+    if (nr16 && (g->radiance != g->normal || g->radiance_pitch != g->normal_pitch))
+        return fail(ctx, SSILVB_ERR_INVALID_ARG, "F16X8: radiance must be the normal plane (same pointer and pitch)");
+    if (nr16 && o->light_out)
+        return fail(ctx, SSILVB_ERR_UNSUPPORTED, "the multi-bounce light buffer needs F32X4 or F16X4 planes");
     const size_t px = g->normal_fmt == SSILVB_FMT_F16X4 ? 8 : 16;
     const size_t W = (size_t)g->width;
     if (g->depth_pitch < W * 4 || g->depth_pitch % 4)
@@ -189,6 +195,7 @@ void fill_params(ssilvb::GatherParams &P, const ssilvb_gbuffer *g, const ssilvb_
     P.hit_rule = p->hit_rule;
     P.step_mode = p->step_mode;
     P.gi = p->compute_gi;
+    P.nr16 = g->normal_fmt == SSILVB_FMT_F16X8 ? 1 : 0;
     const int nb = p->sector_count, nd = p->num_slices, ns = p->steps_per_side, na = p->ambient_cones;
     P.inv_fx = 1.0f / c->fx;
     P.inv_fy = 1.0f / c->fy;
@@ -265,7 +272,7 @@ int batch_occ(int nb, bool f16, bool inf_t, int minb) {
 TuneKey tune_key(const ssilvb_gbuffer *g, const ssilvb_params *p, int batch) {
     TuneKey k;
     k.nb = p->sector_count;
-    k.f16 = g->normal_fmt == SSILVB_FMT_F16X4;
+    k.f16 = half_storage(g->normal_fmt);
     k.inf_t = std::isinf(p->thickness) ? 1 : 0;
     const double px = (double)g->width * g->height;
     k.size_class = (int)std::ceil(std::log2(px > 1.0 ? px : 1.0));
@@ -364,7 +371,7 @@ ssilvb_status ssilvb_gather(ssilvb_ctx *ctx, const ssilvb_gbuffer *gbuffer, cons
     ssilvb::GatherParams P;
     fill_params(P, gbuffer, camera, params, out);
     const KernelChoice k = resolve_choice(ctx, tune_key(gbuffer, params, 0));
-    cudaError_t e = launch_single(P, params->sector_count, gbuffer->normal_fmt == SSILVB_FMT_F16X4,
+    cudaError_t e = launch_single(P, params->sector_count, half_storage(gbuffer->normal_fmt),
                                   std::isinf(params->thickness), k, reinterpret_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "gather launch");
     return SSILVB_OK;

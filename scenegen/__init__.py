@@ -85,6 +85,14 @@ class GBuffer:
         """Exact widening of FP16 planes to FP32."""
         return GBuffer(self.depth, self.normal.astype(np.float32), self.radiance.astype(np.float32), self.camera)
 
+    def interleaved_f16(self) -> np.ndarray:
+        """Normal and radiance in one plane of 8 binary16 per pixel: (n.x, n.y, n.z, c.r, c.g, c.b, 0, 0),
+        the same FP16 values as as_f16() (a storage layout, not a conversion of the data)."""
+        out = np.zeros(self.depth.shape + (8,), dtype=np.float16)
+        out[..., 0:3] = self.normal[..., 0:3].astype(np.float16)
+        out[..., 3:6] = self.radiance[..., 0:3].astype(np.float16)
+        return out
+
 
 def camera_for(width: int, height: int) -> Camera:
     c = np.zeros(13, dtype=np.float32)
