@@ -71,24 +71,24 @@ ssilvb_status ensure_slot(ssilvb_ctx *ctx, BatchSlot &s, int n) {
 }
 
 // The enqueue sequence of one batch: work list host->device, queue counter to zero, kernel.
-cudaError_t enqueue_batch(ssilvb_ctx *ctx, BatchSlot &s, size_t bytes, int nb, bool f16, bool inf_t, int sm,
+cudaError_t enqueue_batch(ssilvb_ctx *ctx, BatchSlot &s, size_t bytes, int nb, int fmt, bool inf_t, int sm,
                           const KernelChoice &k, int grid, cudaStream_t st) {
     const BatchHeader *hdr = reinterpret_cast<const BatchHeader *>(s.d_table);
     const FrameDesc *frames = reinterpret_cast<const FrameDesc *>(s.d_table + sizeof(BatchHeader));
     cudaError_t e = cudaMemcpyAsync(s.d_table, s.h_table, bytes, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(s.d_queue, 0, sizeof(unsigned), st);
-    if (e == cudaSuccess) e = launch_batch_nb(nb, hdr, frames, s.d_queue, f16, inf_t, sm, k, grid, st);
+    if (e == cudaSuccess) e = launch_batch_nb(nb, hdr, frames, s.d_queue, fmt, inf_t, sm, k, grid, st);
     (void)ctx;
     return e;
 }
 
-int occupancy(int nb, bool f16, bool inf_t, int minb) { return batch_occ(nb, f16, inf_t, minb); }
+int occupancy(int nb, int fmt, bool inf_t, int minb) { return batch_occ(nb, fmt, inf_t, minb); }
 
 ssilvb_status run_batch(ssilvb_ctx *ctx, const ssilvb_frame *frames, int n, cudaStream_t st, const KernelChoice *force) {
     if (!frames || n < 1 || n > kMaxFrames)
         return fail(ctx, SSILVB_ERR_INVALID_ARG, "n_frames %d outside 1..%d (or frames NULL)", n, kMaxFrames);
     const int nb = frames[0].params.sector_count;
-    const bool f16 = half_storage(frames[0].gbuffer.normal_fmt);
+    const int fmt = frames[0].gbuffer.normal_fmt;
     const bool inf_t = std::isinf(frames[0].params.thickness);
     const int sm = frames[0].params.step_mode;
     int max_nd = 0, max_ns = 0;
@@ -100,7 +100,7 @@ ssilvb_status run_batch(ssilvb_ctx *ctx, const ssilvb_frame *frames, int n, cuda
             std::string d = ctx->last_error;
             return fail(ctx, s, "frame %d: %s", i, d.c_str());
         }
-        if (f.params.sector_count != nb || half_storage(f.gbuffer.normal_fmt) != f16 ||
+        if (f.params.sector_count != nb || f.gbuffer.normal_fmt != fmt ||
             (bool)std::isinf(f.params.thickness) != inf_t || f.params.step_mode != sm)
             return fail(ctx, SSILVB_ERR_UNSUPPORTED,
                         "frame %d: sector count, storage format, infinite thickness and step mode must match frame 0",
@@ -111,7 +111,7 @@ ssilvb_status run_batch(ssilvb_ctx *ctx, const ssilvb_frame *frames, int n, cuda
     }
     TuneKey key;
     key.nb = nb;
-    key.f16 = f16;
+    key.fmt = fmt;
     key.inf_t = inf_t;
     key.size_class = (int)std::ceil(std::log2(px > 1.0 ? px : 1.0));
     key.nd = max_nd;
@@ -135,7 +135,7 @@ ssilvb_status run_batch(ssilvb_ctx *ctx, const ssilvb_frame *frames, int n, cuda
         auto node_params = [&](int i, cudaKernelNodeParams &kp, void **args) {
             const void *fn = nullptr;
             dim3 grid, block;
-            single_kernel_node(s.fparams[i], nb, f16, inf_t, k, &fn, &grid, &block);
+            single_kernel_node(s.fparams[i], nb, fmt, inf_t, k, &fn, &grid, &block);
             args[0] = &s.fparams[i];
             kp.func = const_cast<void *>(fn);
             kp.gridDim = grid;
@@ -200,20 +200,20 @@ ssilvb_status run_batch(ssilvb_ctx *ctx, const ssilvb_frame *frames, int n, cuda
     hdr->n_frames = n;
     hdr->total_tiles = (int)tiles;
 
-    const int per_sm = k.ctas_per_sm ? k.ctas_per_sm : std::max(1, occupancy(nb, f16, inf_t, k.minb));
+    const int per_sm = k.ctas_per_sm ? k.ctas_per_sm : std::max(1, occupancy(nb, fmt, inf_t, k.minb));
     const int grid = std::max(1, per_sm * ctx->num_sms);  // blocks beyond the work list exit at once
     cudaError_t e;
     if (k.graph) {
         // One cached graph per slot: it always copies the slot's whole table, so it stays valid
         // for any batch that fits; rebuilt only when the slot, kernel variant or grid changes.
-        const auto ek = std::make_tuple(nb, (int)f16, (int)inf_t, sm, k.minb, grid, s.cap);
+        const auto ek = std::make_tuple(nb, fmt, (int)inf_t, sm, k.minb, grid, s.cap);
         if (!s.exec || s.exec_key != ek) {
             if (s.exec) cudaGraphExecDestroy(s.exec);
             s.exec = nullptr;
             cudaGraph_t g = nullptr;
             e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
             if (e == cudaSuccess) {
-                cudaError_t e1 = enqueue_batch(ctx, s, table_bytes(s.cap), nb, f16, inf_t, sm, k, grid, ctx->cap_stream);
+                cudaError_t e1 = enqueue_batch(ctx, s, table_bytes(s.cap), nb, fmt, inf_t, sm, k, grid, ctx->cap_stream);
                 e = cudaStreamEndCapture(ctx->cap_stream, &g);
                 if (e1 != cudaSuccess) e = e1;
             }
@@ -228,7 +228,7 @@ ssilvb_status run_batch(ssilvb_ctx *ctx, const ssilvb_frame *frames, int n, cuda
         }
         e = cudaGraphLaunch(s.exec, st);
     } else {
-        e = enqueue_batch(ctx, s, table_bytes(n), nb, f16, inf_t, sm, k, grid, st);
+        e = enqueue_batch(ctx, s, table_bytes(n), nb, fmt, inf_t, sm, k, grid, st);
     }
     if (e == cudaSuccess) e = cudaEventRecord(s.done, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "batch launch");
@@ -250,7 +250,7 @@ float time_runs(ssilvb_ctx *ctx, const ssilvb_frame *frames, int n, cudaStream_t
             GatherParams P;
             fill_params(P, &frames[0].gbuffer, &frames[0].camera, &frames[0].params, &frames[0].out);
             cudaError_t e = launch_single(P, frames[0].params.sector_count,
-                                          half_storage(frames[0].gbuffer.normal_fmt),
+                                          frames[0].gbuffer.normal_fmt,
                                           std::isinf(frames[0].params.thickness), k, st);
             s = e == cudaSuccess ? SSILVB_OK : cuda_fail(ctx, e, "autotune launch");
         } else {
@@ -343,7 +343,7 @@ ssilvb_status ssilvb_autotune(ssilvb_ctx *ctx, const ssilvb_frame *frames, int n
     }
     TuneKey kb;
     kb.nb = frames[0].params.sector_count;
-    kb.f16 = half_storage(frames[0].gbuffer.normal_fmt);
+    kb.fmt = frames[0].gbuffer.normal_fmt;
     kb.inf_t = std::isinf(frames[0].params.thickness) ? 1 : 0;
     kb.size_class = (int)std::ceil(std::log2(px > 1.0 ? px : 1.0));
     kb.nd = max_nd;

@@ -56,7 +56,6 @@ struct GatherParams {
     int y0, y1;            // centre-pixel rows [y0, y1) this launch covers (samples read the whole frame)
     int nd, ns, na;
     int hit_rule, step_mode, gi;
-    int nr16;              // normal and radiance interleaved: one 16-byte record per pixel (F16X8)
     // per-launch binary32 constants
     float inv_fx, inv_fy, kx0, ninv_fy, ky0;
     float Rfx, dn, K, half_nb, f_nb, inv_nb, inv_nd;
@@ -255,12 +254,17 @@ __device__ __forceinline__ float3 load_xyz(const char *base, size_t pitch, int x
     }
 }
 
-// A sample's normal and radiance: from the two planes, or (F16X8, binary16 only) from its one
-// 16-byte interleaved record (n.x, n.y, n.z, c.r, c.g, c.b, -, -) in a single load.  The values are
-// the same binary16 numbers either way.
-template <bool F16>
+// Storage of normals and radiance, the kernels' FMT parameter (the ABI's format codes): 0 two
+// binary32 planes, 1 two binary16 planes, 2 one interleaved binary16 plane.
+constexpr int kFmtF32 = 0, kFmtF16 = 1, kFmtF16x8 = 2;
+
+// A sample's normal and radiance: from the two planes, or (FMT 2) from its one 16-byte interleaved
+// record (n.x, n.y, n.z, c.r, c.g, c.b, -, -) in a single load.  The values are the same binary16
+// numbers either way.
+template <int FMT>
 __device__ __forceinline__ void load_normal_radiance(const GatherParams &P, int x, int y, float3 &n, float3 &c) {
-    if (F16 && P.nr16) {
+    constexpr bool F16 = FMT != kFmtF32;
+    if (FMT == kFmtF16x8) {
         const uint4 v = __ldg(reinterpret_cast<const uint4 *>(P.normal + (size_t)y * P.normal_pitch) + x);
         const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&v.x));
         const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&v.y));
@@ -274,9 +278,10 @@ __device__ __forceinline__ void load_normal_radiance(const GatherParams &P, int 
 }
 
 // The centre pixel's normal: its plane, or the first half of its interleaved record.
-template <bool F16>
+template <int FMT>
 __device__ __forceinline__ float3 load_normal(const GatherParams &P, int x, int y) {
-    if (F16 && P.nr16) {
+    constexpr bool F16 = FMT != kFmtF32;
+    if (FMT == kFmtF16x8) {
         const uint2 v = __ldg(reinterpret_cast<const uint2 *>(P.normal + (size_t)y * P.normal_pitch) + 2 * x);
         const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&v.x));
         const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&v.y));
@@ -289,8 +294,9 @@ __device__ __forceinline__ float3 load_normal(const GatherParams &P, int x, int 
 __device__ __forceinline__ bool is_geometry(float z) { return __float_as_uint(z) - 1u < 0x7f7fffffu; }
 
 // Multi-bounce epilogue (Section 4.3): the next frame's light = direct + gain * GI.
-template <bool F16>
+template <int FMT>
 __device__ __forceinline__ void write_light(const GatherParams &P, int x, int y, float gr, float gg, float gb) {
+    constexpr bool F16 = FMT != kFmtF32;
     const float3 c = load_xyz<F16>(P.direct, P.direct_pitch, x, y);
     const float r = fmaf(P.gain, gr, c.x), g = fmaf(P.gain, gg, c.y), b = fmaf(P.gain, gb, c.z);
     char *row = P.light_out + (size_t)y * P.light_pitch;
@@ -346,7 +352,7 @@ __device__ __forceinline__ bool endpoints(const GatherParams &P, const Pixel &X,
 // Sector run [A, B] (the back endpoint lies toward this side's edge; a rounding-level reversal gives
 // B < A and no sector), mask update, and the indirect light of the newly occluded sectors
 // (Section 3.3).
-template <int NB, bool F16, bool POS>
+template <int NB, int FMT, bool POS>
 __device__ __forceinline__ void occlude(const GatherParams &P, const Pixel &X, float lx, float ly, float lz, float rl,
                                         float Xf, float Xb, int qx, int qy, typename MaskT<NB>::T &b, float &GIr,
                                         float &GIg, float &GIb) {
@@ -357,7 +363,7 @@ __device__ __forceinline__ void occlude(const GatherParams &P, const Pixel &X, f
     b |= bj;
     if (newly > 0 && P.gi) {
         float3 cj, nj;
-        load_normal_radiance<F16>(P, qx, qy, nj, cj);
+        load_normal_radiance<FMT>(P, qx, qy, nj, cj);
         const float cp = fmaxf(fmaf(X.n.x, lx, fmaf(X.n.y, ly, X.n.z * lz)) * rl, 0.0f);
         const float cq = fmaxf(-(fmaf(nj.x, lx, fmaf(nj.y, ly, nj.z * lz)) * rl), 0.0f);
         const float wgt = (((float)newly * P.inv_nb) * cp) * cq;
@@ -369,7 +375,7 @@ __device__ __forceinline__ void occlude(const GatherParams &P, const Pixel &X, f
 
 // The rest of a step pair's samples that left the cosine band (fa / fb): endpoints, then the mask
 // and indirect light, sample j before sample j + 1.
-template <int NB, bool F16, bool INF_T, bool POS>
+template <int NB, int FMT, bool INF_T, bool POS>
 __device__ __forceinline__ void pair_full(const GatherParams &P, const Pixel &X, bool fa, bool fb, float2 lx,
                                           float2 ly, float2 lz, float2 dv, float2 ll, int qxa, int qya, int qxb,
                                           int qyb, float off, typename MaskT<NB>::T &b, float &GIr, float &GIg,
@@ -378,12 +384,12 @@ __device__ __forceinline__ void pair_full(const GatherParams &P, const Pixel &X,
     if (fa) {
         float rl, Xf, Xb;
         if (endpoints<INF_T, POS>(P, X, dv.x, ll.x, off, rl, Xf, Xb))
-            occlude<NB, F16, POS>(P, X, lx.x, ly.x, lz.x, rl, Xf, Xb, qxa, qya, b, GIr, GIg, GIb);
+            occlude<NB, FMT, POS>(P, X, lx.x, ly.x, lz.x, rl, Xf, Xb, qxa, qya, b, GIr, GIg, GIb);
     }
     if (fb) {
         float rl, Xf, Xb;
         if (endpoints<INF_T, POS>(P, X, dv.y, ll.y, off, rl, Xf, Xb))
-            occlude<NB, F16, POS>(P, X, lx.y, ly.y, lz.y, rl, Xf, Xb, qxb, qyb, b, GIr, GIg, GIb);
+            occlude<NB, FMT, POS>(P, X, lx.y, ly.y, lz.y, rl, Xf, Xb, qxb, qyb, b, GIr, GIg, GIb);
     }
 }
 
@@ -393,7 +399,7 @@ __device__ __forceinline__ void pair_full(const GatherParams &P, const Pixel &X,
 // the indirect light see the samples in the same order as one step at a time.  Once a step leaves
 // the screen every later step of that side does too (the rounded offset is monotone in j, x and
 // y offsets alike, since the noise xi_s is in [0, 1)), so the side ends there.
-template <int NB, bool F16, bool INF_T, int STEP_MODE, bool POS>
+template <int NB, int FMT, bool INF_T, int STEP_MODE, bool POS>
 __device__ __forceinline__ void march_side(const GatherParams &P, const Pixel &X, int x, int y, float cphi,
                                            float sphi, float off, float thr2,
                                            typename MaskT<NB>::T &b, float &GIr, float &GIg, float &GIb) {
@@ -477,7 +483,7 @@ __device__ __forceinline__ void march_side(const GatherParams &P, const Pixel &X
             const float2 dv = pfma(lx, bcast(X.vx), pfma(ly, bcast(X.vy), pmul(lz, bcast(X.vz))));
             const float2 ll = pfma(lx, lx, pfma(ly, ly, pmul(lz, lz)));
             const float2 lim = pmul(bcast(thr2), ll);
-            pair_full<NB, F16, INF_T, POS>(P, X, is_geometry(za) && !(dv.x * fabsf(dv.x) < lim.x),
+            pair_full<NB, FMT, INF_T, POS>(P, X, is_geometry(za) && !(dv.x * fabsf(dv.x) < lim.x),
                                            is_geometry(zb) && !(dv.y * fabsf(dv.y) < lim.y), lx, ly, lz, dv, ll,
                                            qxa, qya, qxb, qyb, off, b, GIr, GIg, GIb);
         }
@@ -519,7 +525,7 @@ __device__ __forceinline__ void march_side(const GatherParams &P, const Pixel &X
         // through the monotone map x -> x |x|) the back endpoint lies still closer to the edge, so
         // no sector is half covered.
         const float2 lim = pmul(bcast(thr2), ll);
-        pair_full<NB, F16, INF_T, POS>(P, X, is_geometry(za) && !(dv.x * fabsf(dv.x) < lim.x),
+        pair_full<NB, FMT, INF_T, POS>(P, X, is_geometry(za) && !(dv.x * fabsf(dv.x) < lim.x),
                                        onb && is_geometry(zb) && !(dv.y * fabsf(dv.y) < lim.y), lx, ly, lz, dv, ll,
                                        qxa, qya, qxb, qyb, off, b, GIr, GIg, GIb);
         if (!onb) break;
@@ -534,7 +540,7 @@ __device__ __forceinline__ void march_side(const GatherParams &P, const Pixel &X
 // STRIDE the block's thread count.  Kept in registers it is live across both step loops, and at 9
 // blocks of 128 threads per SM the register budget then spills; in shared memory it costs a few
 // accesses per slice.  `volatile` keeps each access a real one.
-template <int NB, bool F16, bool INF_T, int STEP_MODE, int STRIDE>
+template <int NB, int FMT, bool INF_T, int STEP_MODE, int STRIDE>
 __device__ __forceinline__ void gather_pixel(const GatherParams &P, int x, int y, volatile float *sl) {
     using M = typename MaskT<NB>::T;
     const float z = __ldg(P.depth + (unsigned)y * (unsigned)P.depth_pitch + (unsigned)x);
@@ -544,7 +550,7 @@ __device__ __forceinline__ void gather_pixel(const GatherParams &P, int x, int y
         if (P.na > 0) *(reinterpret_cast<float4 *>(P.out1 + (size_t)y * P.out1_pitch) + x) = make_float4(0, 0, 0, 0);
         if (P.masks)
             for (int i = 0; i < P.nd; ++i) reinterpret_cast<M *>(P.masks)[((size_t)i * P.H + y) * P.W + x] = 0;
-        if (P.light_out) write_light<F16>(P, x, y, 0.0f, 0.0f, 0.0f);
+        if (P.light_out) write_light<FMT>(P, x, y, 0.0f, 0.0f, 0.0f);
         return;
     }
 
@@ -560,7 +566,7 @@ __device__ __forceinline__ void gather_pixel(const GatherParams &P, int x, int y
     X.vx = -(X.ax * rd);
     X.vy = -(X.by * rd);
     X.vz = rd;
-    X.n = load_normal<F16>(P, x, y);
+    X.n = load_normal<FMT>(P, x, y);
     const float rpx = fminf(P.Rfx / z, 1048576.0f);
     const int cls = (y & 3) * 4 + (x & 3);
     const float xidn = P.xi_s[cls] * P.dn;
@@ -628,9 +634,9 @@ __device__ __forceinline__ void gather_pixel(const GatherParams &P, int x, int y
         sl[7 * STRIDE] = sy;
         sl[8 * STRIDE] = sz;
         // Side -omega, then side +omega (Section 3.3: nearer samples occlude later ones first).
-        march_side<NB, F16, INF_T, STEP_MODE, false>(P, X, x, y, cphi, sphi, off, thr_m * fabsf(thr_m), b,
+        march_side<NB, FMT, INF_T, STEP_MODE, false>(P, X, x, y, cphi, sphi, off, thr_m * fabsf(thr_m), b,
                                                      GIr, GIg, GIb);
-        march_side<NB, F16, INF_T, STEP_MODE, true>(P, X, x, y, cphi, sphi, off, thr_p * fabsf(thr_p), b,
+        march_side<NB, FMT, INF_T, STEP_MODE, true>(P, X, x, y, cphi, sphi, off, thr_p * fabsf(thr_p), b,
                                                     GIr, GIg, GIb);
 
         // Slice end: unoccluded fraction, then the ambient cones (Section 3.2).
@@ -679,20 +685,20 @@ __device__ __forceinline__ void gather_pixel(const GatherParams &P, int x, int y
     }
     const float gr = GIr * P.inv_nd, gg = GIg * P.inv_nd, gb = GIb * P.inv_nd;
     *o0 = make_float4(gr, gg, gb, sl[0] * P.inv_nd);
-    if (P.light_out) write_light<F16>(P, x, y, gr, gg, gb);
+    if (P.light_out) write_light<FMT>(P, x, y, gr, gg, gb);
     if (P.na > 0)
         *(reinterpret_cast<float4 *>(P.out1 + (size_t)y * P.out1_pitch) + x) =
             make_float4(sl[STRIDE] * P.inv_nd, sl[2 * STRIDE] * P.inv_nd, sl[3 * STRIDE] * P.inv_nd, 0.0f);
 }
 
 // Natural mapping: one thread per pixel, 32 x 8 pixel tiles.
-template <int NB, bool F16, bool INF_T, int STEP_MODE>
+template <int NB, int FMT, bool INF_T, int STEP_MODE>
 __global__ void __launch_bounds__(256) gather_tile_kernel(const __grid_constant__ GatherParams P) {
     const int x = blockIdx.x * 32 + (threadIdx.x & 31);
     const int y = P.y0 + blockIdx.y * 8 + (threadIdx.x >> 5);
     if (x >= P.W || y >= P.y1) return;
     __shared__ float slots[kSlots * 256];
-    gather_pixel<NB, F16, INF_T, STEP_MODE, 256>(P, x, y, slots + threadIdx.x);
+    gather_pixel<NB, FMT, INF_T, STEP_MODE, 256>(P, x, y, slots + threadIdx.x);
 }
 
 // Class-strided mapping.  A warp takes 8 x 4 pixels at stride 4 of a 32 x 16 pixel patch, all of
@@ -708,14 +714,14 @@ __device__ __forceinline__ void patch_pixel(int patch_x, int patch_y, int row_cl
     y = patch_y * 16 + 4 * (lane >> 3) + row_class;
 }
 
-template <int NB, bool F16, bool INF_T, int STEP_MODE, int MINB>
+template <int NB, int FMT, bool INF_T, int STEP_MODE, int MINB>
 __global__ void __launch_bounds__(128, MINB) gather_class_kernel(const __grid_constant__ GatherParams P) {
     int x, y;
     patch_pixel(blockIdx.x >> 2, blockIdx.y, blockIdx.x & 3, x, y);
     y += P.y0;
     if (x >= P.W || y >= P.y1) return;
     __shared__ float slots[kSlots * 128];
-    gather_pixel<NB, F16, INF_T, STEP_MODE, 128>(P, x, y, slots + threadIdx.x);
+    gather_pixel<NB, FMT, INF_T, STEP_MODE, 128>(P, x, y, slots + threadIdx.x);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -739,7 +745,7 @@ struct BatchHeader {
     int pad[2];
 };
 
-template <int NB, bool F16, bool INF_T, int STEP_MODE, int MINB>
+template <int NB, int FMT, bool INF_T, int STEP_MODE, int MINB>
 __global__ void __launch_bounds__(128, MINB)
     gather_batch_kernel(const BatchHeader *__restrict__ hdr, const FrameDesc *__restrict__ frames,
                         unsigned *__restrict__ queue) {
@@ -774,7 +780,7 @@ __global__ void __launch_bounds__(128, MINB)
             int x, y;
             patch_pixel(xb >> 2, band * rows + r, xb & 3, x, y);
             if (y >= sP.H) break;
-            if (x < sP.W) gather_pixel<NB, F16, INF_T, STEP_MODE, 128>(sP, x, y, slots + threadIdx.x);
+            if (x < sP.W) gather_pixel<NB, FMT, INF_T, STEP_MODE, 128>(sP, x, y, slots + threadIdx.x);
         }
         __syncthreads();  // everyone is done with s_tile, s_frame and sP before they change
     }

@@ -175,7 +175,7 @@ static ssilvb_status enqueue_frame(ssilvb_ctx *ctx, HostLane &L, const ssilvb_gb
         cudaStream_t ls = L.comp[b & 1];
         P.y0 = (int)y0;
         P.y1 = (int)y1;
-        e = launch_single(P, params->sector_count, half_storage(gbuffer->normal_fmt),
+        e = launch_single(P, params->sector_count, gbuffer->normal_fmt,
                           std::isinf(params->thickness), k, ls);
         if (e == cudaSuccess) e = cudaEventRecord(L.band_done[b], ls);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(L.out, L.band_done[b], 0);

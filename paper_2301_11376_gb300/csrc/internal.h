@@ -39,40 +39,36 @@ struct KernelChoice {
     int batch_mode = 2;              // batch: 1 persistent tile queue, 2 graph of per-frame kernels
 };
 
-// Normal and radiance stored as binary16 (two F16X4 planes or one interleaved F16X8 plane): the
-// kernels' F16 variants.
-inline bool half_storage(int fmt) { return fmt == SSILVB_FMT_F16X4 || fmt == SSILVB_FMT_F16X8; }
-
 // Default register budget of the class and batch kernels (measured at 4K, CUDA events): 8 blocks of
 // 128 threads per SM for N_b = 32 (1 % faster than 9), 9 for N_b = 64 and 128 (1.5 % faster than 8).
 inline int default_minb(int nb) { return nb == 32 ? 8 : 9; }
 
-cudaError_t launch_single_nb32(const GatherParams &P, bool f16, bool inf_t, const KernelChoice &k, cudaStream_t s);
-cudaError_t launch_single_nb64(const GatherParams &P, bool f16, bool inf_t, const KernelChoice &k, cudaStream_t s);
-cudaError_t launch_batch_nb32(const BatchHeader *hdr, const FrameDesc *frames, unsigned *queue, bool f16, bool inf_t,
+cudaError_t launch_single_nb32(const GatherParams &P, int fmt, bool inf_t, const KernelChoice &k, cudaStream_t s);
+cudaError_t launch_single_nb64(const GatherParams &P, int fmt, bool inf_t, const KernelChoice &k, cudaStream_t s);
+cudaError_t launch_batch_nb32(const BatchHeader *hdr, const FrameDesc *frames, unsigned *queue, int fmt, bool inf_t,
                               int step_mode, const KernelChoice &k, int grid, cudaStream_t s);
-cudaError_t launch_batch_nb64(const BatchHeader *hdr, const FrameDesc *frames, unsigned *queue, bool f16, bool inf_t,
+cudaError_t launch_batch_nb64(const BatchHeader *hdr, const FrameDesc *frames, unsigned *queue, int fmt, bool inf_t,
                               int step_mode, const KernelChoice &k, int grid, cudaStream_t s);
-cudaError_t launch_single_nb128(const GatherParams &P, bool f16, bool inf_t, const KernelChoice &k, cudaStream_t s);
-cudaError_t launch_batch_nb128(const BatchHeader *hdr, const FrameDesc *frames, unsigned *queue, bool f16, bool inf_t,
+cudaError_t launch_single_nb128(const GatherParams &P, int fmt, bool inf_t, const KernelChoice &k, cudaStream_t s);
+cudaError_t launch_batch_nb128(const BatchHeader *hdr, const FrameDesc *frames, unsigned *queue, int fmt, bool inf_t,
                                int step_mode, const KernelChoice &k, int grid, cudaStream_t s);
-int batch_occ_nb128(bool f16, bool inf_t, int minb);
-void single_node_nb128(const GatherParams &P, bool f16, bool inf_t, const KernelChoice &k, const void **fn, dim3 *grid,
+int batch_occ_nb128(int fmt, bool inf_t, int minb);
+void single_node_nb128(const GatherParams &P, int fmt, bool inf_t, const KernelChoice &k, const void **fn, dim3 *grid,
                        dim3 *block);
 // Dispatch on the sector count (32, 64 or 128).
-cudaError_t launch_batch_nb(int nb, const BatchHeader *hdr, const FrameDesc *frames, unsigned *queue, bool f16,
+cudaError_t launch_batch_nb(int nb, const BatchHeader *hdr, const FrameDesc *frames, unsigned *queue, int fmt,
                             bool inf_t, int step_mode, const KernelChoice &k, int grid, cudaStream_t s);
-int batch_occ(int nb, bool f16, bool inf_t, int minb);
+int batch_occ(int nb, int fmt, bool inf_t, int minb);
 // The single-frame kernel of a variant and its launch shape (for graph kernel nodes).
-void single_kernel_node(const GatherParams &P, int nb, bool f16, bool inf_t, const KernelChoice &k, const void **fn,
+void single_kernel_node(const GatherParams &P, int nb, int fmt, bool inf_t, const KernelChoice &k, const void **fn,
                         dim3 *grid, dim3 *block);
 // Resident 128-thread blocks per SM of a batch kernel variant (occupancy calculator).
-int batch_occ_nb32(bool f16, bool inf_t, int minb);
-void single_node_nb32(const GatherParams &P, bool f16, bool inf_t, const KernelChoice &k, const void **fn, dim3 *grid,
+int batch_occ_nb32(int fmt, bool inf_t, int minb);
+void single_node_nb32(const GatherParams &P, int fmt, bool inf_t, const KernelChoice &k, const void **fn, dim3 *grid,
                       dim3 *block);
-void single_node_nb64(const GatherParams &P, bool f16, bool inf_t, const KernelChoice &k, const void **fn, dim3 *grid,
+void single_node_nb64(const GatherParams &P, int fmt, bool inf_t, const KernelChoice &k, const void **fn, dim3 *grid,
                       dim3 *block);
-int batch_occ_nb64(bool f16, bool inf_t, int minb);
+int batch_occ_nb64(int fmt, bool inf_t, int minb);
 
 // One in-flight batch: device work list and queue counter, pinned host staging of the work
 // list, the event that marks the batch's kernel done, and its cached CUDA graph.
@@ -93,10 +89,10 @@ struct BatchSlot {
 };
 
 struct TuneKey {
-    int nb, f16, inf_t, size_class, nd, ns, batch;
+    int nb, fmt, inf_t, size_class, nd, ns, batch;  // fmt: the storage format code (ssilvb_format)
     bool operator<(const TuneKey &o) const {
-        return std::tie(nb, f16, inf_t, size_class, nd, ns, batch) <
-               std::tie(o.nb, o.f16, o.inf_t, o.size_class, o.nd, o.ns, o.batch);
+        return std::tie(nb, fmt, inf_t, size_class, nd, ns, batch) <
+               std::tie(o.nb, o.fmt, o.inf_t, o.size_class, o.nd, o.ns, o.batch);
     }
 };
 
@@ -134,7 +130,7 @@ void fill_params(GatherParams &P, const ssilvb_gbuffer *g, const ssilvb_camera *
 TuneKey tune_key(const ssilvb_gbuffer *g, const ssilvb_params *p, int batch);
 // The launch choice for a call: explicit tuning fields win, then autotuned results, then defaults.
 KernelChoice resolve_choice(const ssilvb_ctx *ctx, const TuneKey &key);
-cudaError_t launch_single(const GatherParams &P, int nb, bool f16, bool inf_t, const KernelChoice &k, cudaStream_t s);
+cudaError_t launch_single(const GatherParams &P, int nb, int fmt, bool inf_t, const KernelChoice &k, cudaStream_t s);
 void release_batch_slots(ssilvb_ctx *ctx);
 // Host-buffer paths (host.cu): free their streams, events and staging; wait for asynchronous frames.
 void release_host_resources(ssilvb_ctx *ctx);

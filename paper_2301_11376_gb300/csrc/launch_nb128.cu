@@ -3,20 +3,20 @@
 
 namespace ssilvb {
 
-cudaError_t launch_single_nb128(const GatherParams &P, bool f16, bool inf_t, const KernelChoice &k, cudaStream_t s) {
-    return launch_single_nb<128>(P, f16, inf_t, k, s);
+cudaError_t launch_single_nb128(const GatherParams &P, int fmt, bool inf_t, const KernelChoice &k, cudaStream_t s) {
+    return launch_single_nb<128>(P, fmt, inf_t, k, s);
 }
 
-cudaError_t launch_batch_nb128(const BatchHeader *hdr, const FrameDesc *frames, unsigned *queue, bool f16, bool inf_t,
+cudaError_t launch_batch_nb128(const BatchHeader *hdr, const FrameDesc *frames, unsigned *queue, int fmt, bool inf_t,
                               int step_mode, const KernelChoice &k, int grid, cudaStream_t s) {
-    return launch_batch_nb<128>(hdr, frames, queue, f16, inf_t, step_mode, k, grid, s);
+    return launch_batch_nb<128>(hdr, frames, queue, fmt, inf_t, step_mode, k, grid, s);
 }
 
-int batch_occ_nb128(bool f16, bool inf_t, int minb) { return batch_occ_nb<128>(f16, inf_t, minb); }
+int batch_occ_nb128(int fmt, bool inf_t, int minb) { return batch_occ_nb<128>(fmt, inf_t, minb); }
 
-void single_node_nb128(const GatherParams &P, bool f16, bool inf_t, const KernelChoice &k, const void **fn, dim3 *grid,
+void single_node_nb128(const GatherParams &P, int fmt, bool inf_t, const KernelChoice &k, const void **fn, dim3 *grid,
                      dim3 *block) {
-    single_node_nb<128>(P, f16, inf_t, k, fn, grid, block);
+    single_node_nb<128>(P, fmt, inf_t, k, fn, grid, block);
 }
 
 }  // namespace ssilvb

@@ -70,14 +70,14 @@ extern "C" ssilvb_status ssilvb_gather_batch_noalloc(const ssilvb_frame *frames,
     ssilvb_ctx probe;
     probe.device = dev;
     const int nb = frames[0].params.sector_count;
-    const bool f16 = half_storage(frames[0].gbuffer.normal_fmt);
+    const int fmt = frames[0].gbuffer.normal_fmt;
     const bool inf_t = std::isinf(frames[0].params.thickness);
     const int sm = frames[0].params.step_mode;
     for (int i = 0; i < n_frames; ++i) {
         const ssilvb_frame &f = frames[i];
         st = validate(&probe, &f.gbuffer, &f.camera, &f.params, &f.out, true);
         if (st != SSILVB_OK) return fail(nullptr, st, "frame %d: %s", i, probe.last_error.c_str());
-        if (f.params.sector_count != nb || half_storage(f.gbuffer.normal_fmt) != f16 ||
+        if (f.params.sector_count != nb || f.gbuffer.normal_fmt != fmt ||
             (bool)std::isinf(f.params.thickness) != inf_t || f.params.step_mode != sm)
             return fail(nullptr, SSILVB_ERR_UNSUPPORTED,
                         "frame %d: sector count, storage format, infinite thickness and step mode must match frame 0",
@@ -108,7 +108,7 @@ extern "C" ssilvb_status ssilvb_gather_batch_noalloc(const ssilvb_frame *frames,
     int sms = 0, per_sm = 0;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaDeviceGetAttribute");
-    per_sm = batch_occ(nb, f16, inf_t, k.minb);
+    per_sm = batch_occ(nb, fmt, inf_t, k.minb);
     const int grid = std::max(1, std::max(1, per_sm) * sms);
 
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -122,7 +122,7 @@ extern "C" ssilvb_status ssilvb_gather_batch_noalloc(const ssilvb_frame *frames,
     const BatchHeader *d_hdr = reinterpret_cast<const BatchHeader *>(base);
     const FrameDesc *d_frames = reinterpret_cast<const FrameDesc *>(base + sizeof(BatchHeader));
     unsigned *d_queue = reinterpret_cast<unsigned *>(base + kQueueOffset);
-    e = launch_batch_nb(nb, d_hdr, d_frames, d_queue, f16, inf_t, sm, k, grid, s);
+    e = launch_batch_nb(nb, d_hdr, d_frames, d_queue, fmt, inf_t, sm, k, grid, s);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch launch");
     return SSILVB_OK;
 }

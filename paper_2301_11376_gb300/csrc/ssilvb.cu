@@ -195,7 +195,6 @@ void fill_params(ssilvb::GatherParams &P, const ssilvb_gbuffer *g, const ssilvb_
     P.hit_rule = p->hit_rule;
     P.step_mode = p->step_mode;
     P.gi = p->compute_gi;
-    P.nr16 = g->normal_fmt == SSILVB_FMT_F16X8 ? 1 : 0;
     const int nb = p->sector_count, nd = p->num_slices, ns = p->steps_per_side, na = p->ambient_cones;
     P.inv_fx = 1.0f / c->fx;
     P.inv_fy = 1.0f / c->fy;
@@ -243,36 +242,36 @@ void fill_params(ssilvb::GatherParams &P, const ssilvb_gbuffer *g, const ssilvb_
     P.Y4 = (float)(0.25 * std::sqrt(15.0 / M_PI));
 }
 
-cudaError_t launch_single(const GatherParams &P, int nb, bool f16, bool inf_t, const KernelChoice &k, cudaStream_t s) {
-    if (nb == 32) return launch_single_nb32(P, f16, inf_t, k, s);
-    if (nb == 64) return launch_single_nb64(P, f16, inf_t, k, s);
-    return launch_single_nb128(P, f16, inf_t, k, s);
+cudaError_t launch_single(const GatherParams &P, int nb, int fmt, bool inf_t, const KernelChoice &k, cudaStream_t s) {
+    if (nb == 32) return launch_single_nb32(P, fmt, inf_t, k, s);
+    if (nb == 64) return launch_single_nb64(P, fmt, inf_t, k, s);
+    return launch_single_nb128(P, fmt, inf_t, k, s);
 }
 
-void single_kernel_node(const GatherParams &P, int nb, bool f16, bool inf_t, const KernelChoice &k, const void **fn,
+void single_kernel_node(const GatherParams &P, int nb, int fmt, bool inf_t, const KernelChoice &k, const void **fn,
                         dim3 *grid, dim3 *block) {
-    if (nb == 32) single_node_nb32(P, f16, inf_t, k, fn, grid, block);
-    else if (nb == 64) single_node_nb64(P, f16, inf_t, k, fn, grid, block);
-    else single_node_nb128(P, f16, inf_t, k, fn, grid, block);
+    if (nb == 32) single_node_nb32(P, fmt, inf_t, k, fn, grid, block);
+    else if (nb == 64) single_node_nb64(P, fmt, inf_t, k, fn, grid, block);
+    else single_node_nb128(P, fmt, inf_t, k, fn, grid, block);
 }
 
-cudaError_t launch_batch_nb(int nb, const BatchHeader *hdr, const FrameDesc *frames, unsigned *queue, bool f16,
+cudaError_t launch_batch_nb(int nb, const BatchHeader *hdr, const FrameDesc *frames, unsigned *queue, int fmt,
                             bool inf_t, int step_mode, const KernelChoice &k, int grid, cudaStream_t s) {
-    if (nb == 32) return launch_batch_nb32(hdr, frames, queue, f16, inf_t, step_mode, k, grid, s);
-    if (nb == 64) return launch_batch_nb64(hdr, frames, queue, f16, inf_t, step_mode, k, grid, s);
-    return launch_batch_nb128(hdr, frames, queue, f16, inf_t, step_mode, k, grid, s);
+    if (nb == 32) return launch_batch_nb32(hdr, frames, queue, fmt, inf_t, step_mode, k, grid, s);
+    if (nb == 64) return launch_batch_nb64(hdr, frames, queue, fmt, inf_t, step_mode, k, grid, s);
+    return launch_batch_nb128(hdr, frames, queue, fmt, inf_t, step_mode, k, grid, s);
 }
 
-int batch_occ(int nb, bool f16, bool inf_t, int minb) {
-    if (nb == 32) return batch_occ_nb32(f16, inf_t, minb);
-    if (nb == 64) return batch_occ_nb64(f16, inf_t, minb);
-    return batch_occ_nb128(f16, inf_t, minb);
+int batch_occ(int nb, int fmt, bool inf_t, int minb) {
+    if (nb == 32) return batch_occ_nb32(fmt, inf_t, minb);
+    if (nb == 64) return batch_occ_nb64(fmt, inf_t, minb);
+    return batch_occ_nb128(fmt, inf_t, minb);
 }
 
 TuneKey tune_key(const ssilvb_gbuffer *g, const ssilvb_params *p, int batch) {
     TuneKey k;
     k.nb = p->sector_count;
-    k.f16 = half_storage(g->normal_fmt);
+    k.fmt = g->normal_fmt;
     k.inf_t = std::isinf(p->thickness) ? 1 : 0;
     const double px = (double)g->width * g->height;
     k.size_class = (int)std::ceil(std::log2(px > 1.0 ? px : 1.0));
@@ -371,7 +370,7 @@ ssilvb_status ssilvb_gather(ssilvb_ctx *ctx, const ssilvb_gbuffer *gbuffer, cons
     ssilvb::GatherParams P;
     fill_params(P, gbuffer, camera, params, out);
     const KernelChoice k = resolve_choice(ctx, tune_key(gbuffer, params, 0));
-    cudaError_t e = launch_single(P, params->sector_count, half_storage(gbuffer->normal_fmt),
+    cudaError_t e = launch_single(P, params->sector_count, gbuffer->normal_fmt,
                                   std::isinf(params->thickness), k, reinterpret_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "gather launch");
     return SSILVB_OK;

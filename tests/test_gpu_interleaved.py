@@ -93,15 +93,16 @@ def test_interleaved_host_buffers_and_batch(ctx):
         ctx.gather_host(g.depth, nr, None, g.camera, prm, o0, o1, m, noise=noise, sh=sh, asynchronous=asynchronous)
         ctx.synchronize()
         assert np.array_equal(o0, ref[0]) and np.array_equal(o1, ref[1]) and np.array_equal(m, ref[2])
-    # a batch mixing planar and interleaved frames
+    # a batch of interleaved frames (both launch forms); a batch mixing layouts is refused (the
+    # storage format is a property of the kernel variant, like the sector count)
     d = torch.from_numpy(g.depth).cuda()
     n = torch.from_numpy(g.normal).cuda()
     r = torch.from_numpy(g.radiance).cuda()
     nrd = torch.from_numpy(nr).cuda()
     outs, frames, keep = [], [], None
-    for normal, radiance in ((nrd, None), (n, r), (nrd, None)):
+    for _ in range(3):
         o0, o1, m = ssilvb.alloc_outputs(H, W, prm, "cuda", masks=True)
-        f, keep = ctx.frame(d, normal, radiance, g.camera, prm, o0, o1, m, noise=noise, sh=sh, keep=keep)
+        f, keep = ctx.frame(d, nrd, None, g.camera, prm, o0, o1, m, noise=noise, sh=sh, keep=keep)
         frames.append(f)
         outs.append((o0, o1, m))
     for mode in (1, 2):
@@ -111,6 +112,10 @@ def test_interleaved_host_buffers_and_batch(ctx):
         for o in outs:
             _equal(planar, o)
     ctx.set_tuning()
+    mixed, keep = ctx.frame(d, n, r, g.camera, prm, *outs[0], noise=noise, sh=sh, keep=keep)
+    with pytest.raises(ssilvb.SsilvbError) as ei:
+        ctx.gather_batch([frames[0], mixed])
+    assert ei.value.code == 2
 
 
 def test_interleaved_invalid_arguments(ctx):
