@@ -181,8 +181,11 @@ def _out_bytes(H, W, prm):
 
 
 def _batch_key(pool, req):
-    """What the frames of one ssilvb_gather_batch call must share."""
-    return (req.params.sector_count, str(pool.items[req.key][1].dtype), math.isinf(req.params.thickness),
+    """What the frames of one ssilvb_gather_batch call must share: sector count, storage format (dtype
+    and components of the normal plane: 8 for the interleaved FP16 layout), infinite thickness, step
+    mode."""
+    n = pool.items[req.key][1]
+    return (req.params.sector_count, str(n.dtype), int(n.shape[-1]), math.isinf(req.params.thickness),
             int(getattr(req.params, "step_mode", 0)))
 
 
