@@ -754,6 +754,16 @@ def main():
     clk = clocks.stop()
     ctx.synchronize(stream)
     kern_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    # the same gather with the L2 left warm between steps (reported beside the L2-flushed headline)
+    warm_ms = []
+    for i in range(3 + min(args.steps, 10)):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        if i >= 3:
+            warm_ms.append(a.elapsed_time(b))
     gpu_host = None
     if not args.no_cpu_baseline and rank == 0:  # this workload's outputs, compared on the CPU baseline's pixels
         gpu_host = (out0.cpu().numpy().reshape(-1, 4), out1.cpu().numpy().reshape(-1, 4) if out1 is not None else None)
@@ -894,7 +904,11 @@ def main():
            "layout": ("F16X8 (normal and radiance interleaved)" if interleaved else
                       "F16X4 planes" if g.normal.dtype == np.float16 else "F32X4 planes"),
            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": args.steps,
-           "kernel_ms": {"min": min(kern_ms), "median": statistics.median(kern_ms), "max": max(kern_ms)},
+           "kernel_ms": {"min": min(kern_ms), "p10": float(np.percentile(kern_ms, 10)),
+                         "median": statistics.median(kern_ms), "p90": float(np.percentile(kern_ms, 90)),
+                         "max": max(kern_ms), "l2": "flushed between steps"},
+           "kernel_ms_warm_l2": {"median": statistics.median(warm_ms), "min": min(warm_ms), "steps": len(warm_ms),
+                                 "l2": "not flushed: the G-buffer left in L2 by the previous step"},
            "wall_s_timed_region": wall}
     if extras is not None:
         out.update({k: extras[k] for k in ("sector_counts", "storage_layouts", "batch", "serve") if k in extras})
