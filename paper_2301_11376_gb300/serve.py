@@ -175,9 +175,20 @@ class OutputArena:
         import torch
         return self.buf[off:off + H * W * 16].view(torch.float32).view(H, W, 4)
 
+    def view_masks(self, off, prm, H, W):
+        """Slice bitmasks [N_d, H, W, words] int32 at byte offset off (words = N_b / 32)."""
+        import torch
+        words = prm.sector_count // 32
+        n = prm.num_slices * H * W * words * 4
+        return self.buf[off:off + n].view(torch.int32).view(prm.num_slices, H, W, words)
 
-def _out_bytes(H, W, prm):
-    return H * W * 16 * (2 if prm.ambient_cones > 0 else 1)
+
+def _mask_bytes(H, W, prm):
+    return prm.num_slices * H * W * (prm.sector_count // 32) * 4
+
+
+def _out_bytes(H, W, prm, with_masks=False):
+    return H * W * 16 * (2 if prm.ambient_cones > 0 else 1) + (_mask_bytes(H, W, prm) if with_masks else 0)
 
 
 def _batch_key(pool, req):
@@ -193,14 +204,16 @@ class Server:
     """Continuous batching: batches of arrived requests, several in flight on separate streams."""
 
     def __init__(self, ctx, pool, arena_bytes=1 << 31, max_inflight=4, max_batch=16, max_queue=256, streams=3,
-                 budget_ms=None, rate=4e11, batch_ms=None):
+                 budget_ms=None, rate=4e11, batch_ms=None, with_masks=False):
         """batch_ms: cap on a batch's predicted GPU time (at least one request per batch); None = no cap.
-        With a budget, a request may also wait for the rest of its batch, so admission adds batch_ms."""
+        With a budget, a request may also wait for the rest of its batch, so admission adds batch_ms.
+        with_masks: each request also gets its slice bitmasks, and on_done(req, out0, out1, masks)."""
         import torch
         self.ctx, self.pool = ctx, pool
         self.arena = OutputArena(arena_bytes, pool.device)
         self.max_inflight, self.max_batch, self.max_queue = max_inflight, max_batch, max_queue
         self.budget_ms, self.rate, self.batch_ms = budget_ms, rate, batch_ms
+        self.with_masks = with_masks
         self.streams = [torch.cuda.Stream() for _ in range(streams)]
 
     def run(self, requests, on_done=None, timeout_s=120.0):
@@ -225,7 +238,7 @@ class Server:
                 req = reqs[i]
                 H, W = self.pool.shape(req.key)
                 # a request whose outputs exceed the whole arena could never be launched: shed it
-                fits = _out_bytes(H, W, req.params) <= self.arena.size
+                fits = _out_bytes(H, W, req.params, self.with_masks) <= self.arena.size
                 if fits and adm.admit(now, req.arrival, request_samples(H, W, req.params)):
                     pending.append(req)
                 else:
@@ -237,7 +250,7 @@ class Server:
                 t_done = time.perf_counter() - t0
                 adm.observe(bsamples, t_done - max(t_launch, last_done))
                 last_done = t_done
-                for req, off, nb_, o0, o1, smp in items:
+                for req, off, nb_, o0, o1, mk, smp in items:
                     lat = t_done - req.arrival
                     st.latencies_ms.append(lat * 1e3)
                     st.served += 1
@@ -245,7 +258,10 @@ class Server:
                     st.samples_within_budget += smp if lat <= budget_s else 0
                     adm.done(smp)
                     if on_done is not None:
-                        on_done(req, o0, o1)
+                        if self.with_masks:
+                            on_done(req, o0, o1, mk)
+                        else:
+                            on_done(req, o0, o1)
                     self.arena.release(off, nb_)
             # admit and launch the next batch
             if pending and len(inflight) < self.max_inflight:
@@ -264,7 +280,7 @@ class Server:
                         skipped.append(req)  # the batch's span is full: the request leads the next one
                         break
                     work += request_samples(H, W, req.params)
-                    nbytes = _out_bytes(H, W, req.params)
+                    nbytes = _out_bytes(H, W, req.params, self.with_masks)
                     got = self.arena.alloc(nbytes)
                     if got is None:  # wait for memory: keep the request at its place in the queue
                         skipped.append(req)
@@ -272,11 +288,14 @@ class Server:
                     off, nb_ = got
                     o0 = self.arena.view(off, H, W)
                     o1 = self.arena.view(off + H * W * 16, H, W) if req.params.ambient_cones > 0 else None
+                    mk = None
+                    if self.with_masks:
+                        mk = self.arena.view_masks(off + _out_bytes(H, W, req.params), req.params, H, W)
                     d, n, r, cam = self.pool.items[req.key]
-                    f, keep = self.ctx.frame(d, n, r, cam, req.params, o0, o1, None, noise=req.noise, sh=req.sh,
+                    f, keep = self.ctx.frame(d, n, r, cam, req.params, o0, o1, mk, noise=req.noise, sh=req.sh,
                                              keep=keep)
                     frames.append(f)
-                    batch.append((req, off, nb_, o0, o1, request_samples(H, W, req.params)))
+                    batch.append((req, off, nb_, o0, o1, mk, request_samples(H, W, req.params)))
                 while skipped:
                     pending.appendleft(skipped.pop())
                 if batch:
@@ -293,7 +312,7 @@ class Server:
                         raise
                     ev = torch.cuda.Event()
                     ev.record(s)
-                    bsamples = sum(b[5] for b in batch)
+                    bsamples = sum(b[6] for b in batch)
                     inflight.append((ev, time.perf_counter() - t0, bsamples, batch))
                     st.samples += bsamples
                     st.batches += 1

@@ -36,12 +36,13 @@ def test_serving_results_equal_alone():
             q.params = dataclasses.replace(q.params, thickness=math.inf)
         if q.rid % 7 == 2:
             q.params = dataclasses.replace(q.params, step_mode=1)
-    got = {}
+    got, got_masks = {}, {}
 
-    def keep(req, o0, o1):
+    def keep(req, o0, o1, masks):
         got[req.rid] = o0.clone()
+        got_masks[req.rid] = masks.clone()
 
-    srv = serve.Server(ctx, pool, arena_bytes=64 << 20, max_inflight=4, max_batch=8)
+    srv = serve.Server(ctx, pool, arena_bytes=96 << 20, max_inflight=4, max_batch=8, with_masks=True)
     st = srv.run(reqs, on_done=keep)
     torch.cuda.synchronize()
     assert st.served == len(reqs) and st.dropped == 0
@@ -50,13 +51,14 @@ def test_serving_results_equal_alone():
     for req in reqs:
         d, n, r, cam = pool.items[req.key]
         H, W = d.shape
-        o0, _, _ = ssilvb.alloc_outputs(H, W, req.params, "cuda")
-        ctx.gather(d, n, r, cam, req.params, o0, None, None, noise=req.noise)
+        o0, _, m = ssilvb.alloc_outputs(H, W, req.params, "cuda", masks=True)
+        ctx.gather(d, n, r, cam, req.params, o0, None, m, noise=req.noise)
         torch.cuda.synchronize()
         assert torch.equal(got[req.rid], o0), req.rid
-        # the served result against the oracle (no masks in serving: outputs only)
-        check_tensors(host[req.key], req.params, req.noise, None, got[req.rid], n_sample=3000, seed=req.rid,
-                      min_clear=0.5)  # up to 8 slices: fewer pixels clear in every slice
+        assert torch.equal(got_masks[req.rid], m), req.rid  # masks bit-exact alone and in the mix
+        # the served result against the oracle: masks against the replica, outputs against FP64
+        check_tensors(host[req.key], req.params, req.noise, None, got[req.rid], None, got_masks[req.rid],
+                      n_sample=3000, seed=req.rid, min_clear=0.5)  # up to 8 slices: fewer pixels clear in every slice
     # the naive baseline serves the same results
     got_plain = {}
     plain = serve.PlainServer(ctx, pool)
