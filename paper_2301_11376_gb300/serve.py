@@ -126,11 +126,17 @@ class ResidentPool:
         self.device = device
         self.items = {}
 
-    def add(self, key, gbuf):
+    def add(self, key, gbuf, interleaved=False):
+        """Make gbuf resident.  interleaved: store FP16 normal and radiance as one interleaved plane
+        (F16X8; the radiance entry is then None)."""
         import torch
         d = torch.from_numpy(np.ascontiguousarray(gbuf.depth)).to(self.device)
-        n = torch.from_numpy(np.ascontiguousarray(gbuf.normal)).to(self.device)
-        r = torch.from_numpy(np.ascontiguousarray(gbuf.radiance)).to(self.device)
+        if interleaved:
+            n = torch.from_numpy(gbuf.interleaved_f16()).to(self.device)
+            r = None
+        else:
+            n = torch.from_numpy(np.ascontiguousarray(gbuf.normal)).to(self.device)
+            r = torch.from_numpy(np.ascontiguousarray(gbuf.radiance)).to(self.device)
         self.items[key] = (d, n, r, gbuf.camera)
 
     def shape(self, key):
