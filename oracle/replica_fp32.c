@@ -53,9 +53,11 @@ static const float kHalfPi32 = 1.57079637050628662109375f;
                                  empty test 1, two low-bit masks 6, and-not 2 (per extra word +4);
                                  newly: not, and, popcount (two words: 7); or; GI test 2 */
 #define OPS_GI 17             /* two clamped cosines 10, weight 4, three fma */
-#define OPS_CONE(W) (11 + 4 * ((W) - 1) + 4 + 6 + 9 + 15 + 2 + 27 + 3 + 2)
-                              /* group mask and count 11, direction 10, world 9, SH basis 15,
-                                 weight 2, three 9-term sums 27, accumulate 3, loop 2 */
+#define OPS_CONE(W) (11 + 4 * ((W) - 1) + 4 + 2 + 2 + 5 + 2)
+                              /* group mask and count 11, direction 4, weight 2, weighted
+                                 cosine and sine 2, five sums 5, loop 2 */
+#define OPS_AMB_SLICE 80      /* doubled sum 1, u 6, b.u 9, doublings 4, monomials 21,
+                                 t_m 18, q_m t_m 18, accumulate 3 */
 
 /* Abramowitz and Stegun 4.4.46 coefficients a0..a7. */
 static const float AS0 = 1.5707963050f, AS1 = -0.2145988016f, AS2 = 0.0889789874f, AS3 = -0.0501743046f;
@@ -155,8 +157,47 @@ typedef struct {
     float edge_hi, edge_lo, sdel, cdel;
     float dcos[16][16], dsin[16][16];
     float ccos[8], csin[8];
-    float Y0, Y1, Y2, Y3, Y4;
+    float amb_b[3][3], amb_q[3][6]; /* the SH environment as L(a) = b.a + a^T Q a, view space */
 } ctx32;
+
+/* The 3-band SH environment (sh[3 m + channel], m the real SH basis y00, y1-1, y10, y11, y2-2,
+ * y2-1, y20, y21, y22) as a quadratic form of the view-space direction a.  For a unit world direction
+ * w = R a the sum of sh_m Y_m(w) is c + b_w.w + w^T M w, with c = Y00 sh0 - (Y20's constant term)
+ * sh6, b_w = Y1 (sh3, sh1, sh2) and M the band-2 terms; c goes on the diagonal (c |a|^2 = c), so
+ * b = R^T b_w and Q = R^T M R + c I.  FP64, each coefficient rounded once to binary32; Q is kept as
+ * (xx, yy, zz, xy, xz, yz). */
+static void ambient_form32(const float *R, const float *sh, float b_out[3][3], float q_out[3][6]) {
+    const double y0 = 0.5 * sqrt(1.0 / M_PI), y1 = sqrt(3.0 / (4.0 * M_PI));
+    const double y2 = 0.5 * sqrt(15.0 / M_PI), y3 = 0.25 * sqrt(5.0 / M_PI);
+    const double y4 = 0.25 * sqrt(15.0 / M_PI);
+    double Rd[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) Rd[i][j] = (double)R[3 * i + j];
+    for (int ch = 0; ch < 3; ++ch) {
+        double h[9];
+        for (int m = 0; m < 9; ++m) h[m] = (double)sh[3 * m + ch];
+        const double cc = y0 * h[0] - y3 * h[6];
+        const double bw[3] = {y1 * h[3], y1 * h[1], y1 * h[2]};
+        const double Mw[3][3] = {{y4 * h[8], 0.5 * y2 * h[4], 0.5 * y2 * h[7]},
+                                 {0.5 * y2 * h[4], -(y4 * h[8]), 0.5 * y2 * h[5]},
+                                 {0.5 * y2 * h[7], 0.5 * y2 * h[5], 3.0 * y3 * h[6]}};
+        double T[3][3], Q[3][3];
+        for (int i = 0; i < 3; ++i)
+            for (int k = 0; k < 3; ++k) T[i][k] = (Mw[i][0] * Rd[0][k] + Mw[i][1] * Rd[1][k]) + Mw[i][2] * Rd[2][k];
+        for (int j = 0; j < 3; ++j)
+            for (int k = 0; k < 3; ++k) Q[j][k] = (Rd[0][j] * T[0][k] + Rd[1][j] * T[1][k]) + Rd[2][j] * T[2][k];
+        for (int j = 0; j < 3; ++j) {
+            b_out[ch][j] = (float)((Rd[0][j] * bw[0] + Rd[1][j] * bw[1]) + Rd[2][j] * bw[2]);
+            Q[j][j] = Q[j][j] + cc;
+        }
+        q_out[ch][0] = (float)Q[0][0];
+        q_out[ch][1] = (float)Q[1][1];
+        q_out[ch][2] = (float)Q[2][2];
+        q_out[ch][3] = (float)Q[0][1];
+        q_out[ch][4] = (float)Q[0][2];
+        q_out[ch][5] = (float)Q[1][2];
+    }
+}
 
 static void setup32(const orc_problem *pb, ctx32 *c) {
     c->W = pb->width;
@@ -204,11 +245,7 @@ static void setup32(const orc_problem *pb, ctx32 *c) {
         c->ccos[k] = (float)cos(th);
         c->csin[k] = (float)sin(th);
     }
-    c->Y0 = (float)(0.5 * sqrt(1.0 / M_PI));
-    c->Y1 = (float)sqrt(3.0 / (4.0 * M_PI));
-    c->Y2 = (float)(0.5 * sqrt(15.0 / M_PI));
-    c->Y3 = (float)(0.25 * sqrt(5.0 / M_PI));
-    c->Y4 = (float)(0.25 * sqrt(15.0 / M_PI));
+    if (c->na > 0) ambient_form32(pb->view_to_world, pb->sh, c->amb_b, c->amb_q);
 }
 
 /* One pixel of the replica.  cnt[7] accumulates the counters of orc32_pixels.  runs (may be NULL):
@@ -397,38 +434,45 @@ static void pixel32(const orc_problem *pb, const ctx32 *c, int x, int y, float *
         const int occ = popc128(b);
         AO += (float)(nb - occ) * c->inv_nb;
         ops += 5;
-        for (int k = 0; k < na; ++k) {
+        if (na > 0) {
+            /* Cone k's direction is a_k = c_k v + s_k s and the environment is L(a) = b.a + a^T Q a,
+             * so sum_k w_k L(a_k) = b.u + sum_m q_m t_m: u = v sum w c + s sum w s, and t_m = (v's
+             * monomial m) sum w c^2 + (s's) sum w s^2 + (the symmetric product's) 2 sum w c s. */
             const int g = nb / na;
-            const mask_t Mk = low_bits((k + 1) * g) & ~low_bits(k * g);
-            const int freek = popc128(~b & Mk);
-            const float ck = fmaf(cg, c->ccos[k], -(sg * c->csin[k]));
-            const float sk = fmaf(sg, c->ccos[k], cg * c->csin[k]);
-            const float ax3 = fmaf(ck, vx, sk * sx), ay3 = fmaf(ck, vy, sk * sy), az3 = fmaf(ck, vz, sk * sz);
-            const float *R = pb->view_to_world;
-            const float wx = fmaf(R[0], ax3, fmaf(R[1], ay3, R[2] * az3));
-            const float wy = fmaf(R[3], ax3, fmaf(R[4], ay3, R[5] * az3));
-            const float wz = fmaf(R[6], ax3, fmaf(R[7], ay3, R[8] * az3));
-            float Y[9];
-            Y[0] = c->Y0;
-            Y[1] = c->Y1 * wy;
-            Y[2] = c->Y1 * wz;
-            Y[3] = c->Y1 * wx;
-            Y[4] = c->Y2 * (wx * wy);
-            Y[5] = c->Y2 * (wy * wz);
-            Y[6] = c->Y3 * fmaf(3.0f * wz, wz, -1.0f);
-            Y[7] = c->Y2 * (wx * wz);
-            Y[8] = c->Y4 * fmaf(wx, wx, -(wy * wy));
-            const float wt = (float)freek * c->inv_nb;
-            float L[3];
-            for (int ch = 0; ch < 3; ++ch) {
-                float acc = pb->sh[ch] * Y[0];
-                for (int m = 1; m < 9; ++m) acc = fmaf(pb->sh[3 * m + ch], Y[m], acc);
-                L[ch] = acc;
+            float Wc = 0.0f, Ws = 0.0f, Wcc = 0.0f, Wss = 0.0f, Wcs = 0.0f;
+            for (int k = 0; k < na; ++k) {
+                const mask_t Mk = low_bits((k + 1) * g) & ~low_bits(k * g);
+                const int freek = popc128(~b & Mk);
+                const float ck = fmaf(cg, c->ccos[k], -(sg * c->csin[k]));
+                const float sk = fmaf(sg, c->ccos[k], cg * c->csin[k]);
+                const float wt = (float)freek * c->inv_nb;
+                const float tc = wt * ck, ts = wt * sk;
+                Wc = Wc + tc;
+                Ws = Ws + ts;
+                Wcc = fmaf(tc, ck, Wcc);
+                Wss = fmaf(ts, sk, Wss);
+                Wcs = fmaf(tc, sk, Wcs);
+                ops += c->ops_cone;
             }
-            AMr = fmaf(wt, L[0], AMr);
-            AMg = fmaf(wt, L[1], AMg);
-            AMb = fmaf(wt, L[2], AMb);
-            ops += c->ops_cone;
+            const float W2cs = Wcs + Wcs;
+            const float ux = fmaf(vx, Wc, sx * Ws), uy = fmaf(vy, Wc, sy * Ws), uz = fmaf(vz, Wc, sz * Ws);
+            float acc[3];
+            for (int ch = 0; ch < 3; ++ch)
+                acc[ch] = fmaf(c->amb_b[ch][2], uz, fmaf(c->amb_b[ch][1], uy, c->amb_b[ch][0] * ux));
+            const float vx2 = vx + vx, vy2 = vy + vy, sx2 = sx + sx, sy2 = sy + sy;
+            /* monomials of Q's entries xx, yy, zz, xy, xz, yz: of v, of s, and of the pair (v, s) */
+            const float pv[6] = {vx * vx, vy * vy, vz * vz, vx2 * vy, vx2 * vz, vy2 * vz};
+            const float ps[6] = {sx * sx, sy * sy, sz * sz, sx2 * sy, sx2 * sz, sy2 * sz};
+            const float pc[6] = {vx * sx, vy * sy, vz * sz, fmaf(vx, sy, vy * sx), fmaf(vx, sz, vz * sx),
+                                 fmaf(vy, sz, vz * sy)};
+            for (int m = 0; m < 6; ++m) {
+                const float t = fmaf(pv[m], Wcc, fmaf(ps[m], Wss, pc[m] * W2cs));
+                for (int ch = 0; ch < 3; ++ch) acc[ch] = fmaf(c->amb_q[ch][m], t, acc[ch]);
+            }
+            AMr = AMr + acc[0];
+            AMg = AMg + acc[1];
+            AMb = AMb + acc[2];
+            ops += OPS_AMB_SLICE;
         }
         if (mk) {
             mk[(size_t)i * words] = (uint64_t)b;

@@ -66,9 +66,10 @@ struct GatherParams {
     float dcos[16][kMaxSlices];
     float dsin[16][kMaxSlices];
     float ccos[kMaxCones], csin[kMaxCones];
-    float R[9];
-    float sh[27];
-    float Y0, Y1, Y2, Y3, Y4;
+    // The SH environment as a quadratic form of the view-space direction a: L(a) = b.a + a^T Q a
+    // per channel, Q as (xx, yy, zz, xy, xz, yz) (Section 3.2's ambient light, 3 SH bands).
+    float amb_b[3][3];
+    float amb_q[3][6];
 };
 
 // Packed binary32 pairs (add/sub/mul/fma.rn.f32x2).  Each half is one IEEE binary32 operation
@@ -642,44 +643,55 @@ __device__ __forceinline__ void gather_pixel(const GatherParams &P, int x, int y
         // Slice end: unoccluded fraction, then the ambient cones (Section 3.2).
         sl[0] = sl[0] + (float)(NB - popc_(b)) * P.inv_nb;
         if (P.na > 0) {
+            // Cone k's direction is a_k = c_k v + s_k s (c_k, s_k the cosine and sine of its angle from
+            // v in the slice plane) and the environment is a quadratic form of a unit direction,
+            // L(a) = b.a + a^T Q a.  The weighted sum over the cones, sum_k w_k L(a_k), is therefore
+            // b.u + sum over Q's six entries of q_m t_m, with u = v sum w c + s sum w s and t_m the
+            // entry's monomial of v times sum w c^2, plus that of s times sum w s^2, plus the symmetric
+            // product of v and s times 2 sum w c s: five channel-independent sums over the cones.
             const float cg = sl[4 * STRIDE], sg = sl[5 * STRIDE];
-            const float sx = sl[6 * STRIDE], sy = sl[7 * STRIDE], sz = sl[8 * STRIDE];
-            float AMr = sl[STRIDE], AMg = sl[2 * STRIDE], AMb = sl[3 * STRIDE];
             const int g = NB / P.na;
+            float Wc = 0.0f, Ws = 0.0f, Wcc = 0.0f, Wss = 0.0f, Wcs = 0.0f;
+#pragma unroll 1
             for (int k = 0; k < P.na; ++k) {
                 const M Mk = run_mask<NB>(k * g, (k + 1) * g);
                 const int freek = popc_(~b & Mk);
                 const float ck = fmaf(cg, P.ccos[k], -(sg * P.csin[k]));
                 const float sk = fmaf(sg, P.ccos[k], cg * P.csin[k]);
-                const float a3x = fmaf(ck, X.vx, sk * sx), a3y = fmaf(ck, X.vy, sk * sy), a3z = fmaf(ck, X.vz, sk * sz);
-                const float wx = fmaf(P.R[0], a3x, fmaf(P.R[1], a3y, P.R[2] * a3z));
-                const float wy = fmaf(P.R[3], a3x, fmaf(P.R[4], a3y, P.R[5] * a3z));
-                const float wz = fmaf(P.R[6], a3x, fmaf(P.R[7], a3y, P.R[8] * a3z));
-                float Y[9];
-                Y[0] = P.Y0;
-                Y[1] = P.Y1 * wy;
-                Y[2] = P.Y1 * wz;
-                Y[3] = P.Y1 * wx;
-                Y[4] = P.Y2 * (wx * wy);
-                Y[5] = P.Y2 * (wy * wz);
-                Y[6] = P.Y3 * fmaf(3.0f * wz, wz, -1.0f);
-                Y[7] = P.Y2 * (wx * wz);
-                Y[8] = P.Y4 * fmaf(wx, wx, -(wy * wy));
                 const float wt = (float)freek * P.inv_nb;
-                float L0 = P.sh[0] * Y[0], L1 = P.sh[1] * Y[0], L2 = P.sh[2] * Y[0];
-#pragma unroll
-                for (int m = 1; m < 9; ++m) {
-                    L0 = fmaf(P.sh[3 * m + 0], Y[m], L0);
-                    L1 = fmaf(P.sh[3 * m + 1], Y[m], L1);
-                    L2 = fmaf(P.sh[3 * m + 2], Y[m], L2);
-                }
-                AMr = fmaf(wt, L0, AMr);
-                AMg = fmaf(wt, L1, AMg);
-                AMb = fmaf(wt, L2, AMb);
+                const float tc = wt * ck, ts = wt * sk;
+                Wc = Wc + tc;
+                Ws = Ws + ts;
+                Wcc = fmaf(tc, ck, Wcc);
+                Wss = fmaf(ts, sk, Wss);
+                Wcs = fmaf(tc, sk, Wcs);
             }
-            sl[STRIDE] = AMr;
-            sl[2 * STRIDE] = AMg;
-            sl[3 * STRIDE] = AMb;
+            const float W2cs = Wcs + Wcs;
+            const float sx = sl[6 * STRIDE], sy = sl[7 * STRIDE], sz = sl[8 * STRIDE];
+            const float ux = fmaf(X.vx, Wc, sx * Ws), uy = fmaf(X.vy, Wc, sy * Ws), uz = fmaf(X.vz, Wc, sz * Ws);
+            float acc[3];
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) acc[ch] = fmaf(P.amb_b[ch][2], uz, fmaf(P.amb_b[ch][1], uy, P.amb_b[ch][0] * ux));
+            const float vx2 = X.vx + X.vx, vy2 = X.vy + X.vy, sx2 = sx + sx, sy2 = sy + sy;
+#pragma unroll
+            for (int m = 0; m < 6; ++m) {
+                // Q's entries xx, yy, zz, xy, xz, yz: squares, doubled products, symmetric sums
+                float pv, ps, pc;
+                switch (m) {
+                case 0: pv = X.vx * X.vx; ps = sx * sx; pc = X.vx * sx; break;
+                case 1: pv = X.vy * X.vy; ps = sy * sy; pc = X.vy * sy; break;
+                case 2: pv = X.vz * X.vz; ps = sz * sz; pc = X.vz * sz; break;
+                case 3: pv = vx2 * X.vy; ps = sx2 * sy; pc = fmaf(X.vx, sy, X.vy * sx); break;
+                case 4: pv = vx2 * X.vz; ps = sx2 * sz; pc = fmaf(X.vx, sz, X.vz * sx); break;
+                default: pv = vy2 * X.vz; ps = sy2 * sz; pc = fmaf(X.vy, sz, X.vz * sy); break;
+                }
+                const float t = fmaf(pv, Wcc, fmaf(ps, Wss, pc * W2cs));
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) acc[ch] = fmaf(P.amb_q[ch][m], t, acc[ch]);
+            }
+            sl[STRIDE] = sl[STRIDE] + acc[0];
+            sl[2 * STRIDE] = sl[2 * STRIDE] + acc[1];
+            sl[3 * STRIDE] = sl[3 * STRIDE] + acc[2];
         }
         if (P.masks) reinterpret_cast<M *>(P.masks)[((size_t)i * P.H + y) * P.W + x] = b;
     }

@@ -163,6 +163,45 @@ static void builtin_noise(int frame, float table[32]) {
         }
 }
 
+// The 3-band SH environment (coefficients sh[3 m + channel], m the real SH basis y00, y1-1, y10,
+// y11, y2-2, y2-1, y20, y21, y22 with the usual normalisation) as a quadratic form of the view-space
+// direction a (Section 3.2's ambient light).  For a unit world direction w = R a the sum of
+// sh_m Y_m(w) is c + b_w.w + w^T M w: c holds band 0 and the constant term of y20, b_w = Y1 (sh3,
+// sh1, sh2) band 1, M band 2.  The constant goes on the diagonal (c |a|^2 = c), so b = R^T b_w and
+// Q = R^T M R + c I.  FP64, each coefficient rounded once to binary32; Q kept as (xx, yy, zz, xy, xz, yz).
+static void ambient_form(const float R[9], const float *sh, float b_out[3][3], float q_out[3][6]) {
+    const double y0 = 0.5 * std::sqrt(1.0 / M_PI), y1 = std::sqrt(3.0 / (4.0 * M_PI));
+    const double y2 = 0.5 * std::sqrt(15.0 / M_PI), y3 = 0.25 * std::sqrt(5.0 / M_PI);
+    const double y4 = 0.25 * std::sqrt(15.0 / M_PI);
+    double Rd[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) Rd[i][j] = (double)R[3 * i + j];
+    for (int ch = 0; ch < 3; ++ch) {
+        double h[9];
+        for (int m = 0; m < 9; ++m) h[m] = (double)sh[3 * m + ch];
+        const double c = y0 * h[0] - y3 * h[6];
+        const double bw[3] = {y1 * h[3], y1 * h[1], y1 * h[2]};
+        const double Mw[3][3] = {{y4 * h[8], 0.5 * y2 * h[4], 0.5 * y2 * h[7]},
+                                 {0.5 * y2 * h[4], -(y4 * h[8]), 0.5 * y2 * h[5]},
+                                 {0.5 * y2 * h[7], 0.5 * y2 * h[5], 3.0 * y3 * h[6]}};
+        double T[3][3], Q[3][3];
+        for (int i = 0; i < 3; ++i)
+            for (int k = 0; k < 3; ++k) T[i][k] = (Mw[i][0] * Rd[0][k] + Mw[i][1] * Rd[1][k]) + Mw[i][2] * Rd[2][k];
+        for (int j = 0; j < 3; ++j)
+            for (int k = 0; k < 3; ++k) Q[j][k] = (Rd[0][j] * T[0][k] + Rd[1][j] * T[1][k]) + Rd[2][j] * T[2][k];
+        for (int j = 0; j < 3; ++j) {
+            b_out[ch][j] = (float)((Rd[0][j] * bw[0] + Rd[1][j] * bw[1]) + Rd[2][j] * bw[2]);
+            Q[j][j] = Q[j][j] + c;
+        }
+        q_out[ch][0] = (float)Q[0][0];
+        q_out[ch][1] = (float)Q[1][1];
+        q_out[ch][2] = (float)Q[2][2];
+        q_out[ch][3] = (float)Q[0][1];
+        q_out[ch][4] = (float)Q[0][2];
+        q_out[ch][5] = (float)Q[1][2];
+    }
+}
+
 // Per-launch constants.  Every expression is written out exactly as the method's binary32
 // specification fixes it (the same expressions any other IEEE implementation evaluates).
 void fill_params(ssilvb::GatherParams &P, const ssilvb_gbuffer *g, const ssilvb_camera *c, const ssilvb_params *p,
@@ -232,14 +271,7 @@ void fill_params(ssilvb::GatherParams &P, const ssilvb_gbuffer *g, const ssilvb_
         P.ccos[k] = (float)std::cos(th);
         P.csin[k] = (float)std::sin(th);
     }
-    for (int i = 0; i < 9; ++i) P.R[i] = c->view_to_world[i];
-    if (na > 0)
-        for (int i = 0; i < 27; ++i) P.sh[i] = p->sh_rgb[i];
-    P.Y0 = (float)(0.5 * std::sqrt(1.0 / M_PI));
-    P.Y1 = (float)std::sqrt(3.0 / (4.0 * M_PI));
-    P.Y2 = (float)(0.5 * std::sqrt(15.0 / M_PI));
-    P.Y3 = (float)(0.25 * std::sqrt(5.0 / M_PI));
-    P.Y4 = (float)(0.25 * std::sqrt(15.0 / M_PI));
+    if (na > 0) ambient_form(c->view_to_world, p->sh_rgb, P.amb_b, P.amb_q);
 }
 
 cudaError_t launch_single(const GatherParams &P, int nb, int fmt, bool inf_t, const KernelChoice &k, cudaStream_t s) {
