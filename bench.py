@@ -784,9 +784,10 @@ def main():
         # next frame's gather); every step still copies its inputs in and its outputs back
         outs = [(ho0, ho1), (torch.empty_like(ho0).pin_memory(),
                              torch.empty_like(ho1).pin_memory() if ho1 is not None else None)]
-        for i in range(2):  # warm-up: the staging of the synchronous lane and of both pipelined lanes
-            ctx.gather_host(hd, hn, hr, g.camera, w.params, ho0, ho1, None, noise=w.noise, sh=w.sh, stream=stream)
-            ctx.gather_host(hd, hn, hr, g.camera, w.params, *outs[i], None, noise=w.noise, sh=w.sh, stream=stream,
+        # warm-up: the staging of the synchronous lane, then W frames through both pipelined lanes
+        ctx.gather_host(hd, hn, hr, g.camera, w.params, ho0, ho1, None, noise=w.noise, sh=w.sh, stream=stream)
+        for i in range(max(2, args.warmup)):
+            ctx.gather_host(hd, hn, hr, g.camera, w.params, *outs[i % 2], None, noise=w.noise, sh=w.sh, stream=stream,
                             asynchronous=True)
         ctx.synchronize(stream)
         ke = max(3, args.steps)  # the same number of frames as the device-timed region
