@@ -425,7 +425,8 @@ def batch_measure(ctx, dev, steps, warmup, base_seed=1000, world=1, sizes=None):
            "samples_per_batch": samples, "steps": steps, "warmup": warmup,
            "l2": "flushed (256 MB write) between timed steps",
            "tuning": {"occupancy": tuned.occupancy, "rows_per_tile": tuned.rows_per_tile,
-                      "use_graph": tuned.use_graph, "batch_mode": tuned.batch_mode},
+                      "use_graph": tuned.use_graph, "batch_mode": tuned.batch_mode,
+                      "block_order": tuned.block_order},
            "accuracy": "each frame bit-identical to its single-frame gather; masks bit-exact against the binary32 "
                        "replica and outputs within 1e-4 of FP64 (tests/test_gpu_batch.py)"}
     for name, m in med.items():

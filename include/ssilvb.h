@@ -164,7 +164,11 @@ typedef struct {
     int use_graph;        /* batch, persistent mode: 0 auto, 1 launch through a cached CUDA graph, 2 plain */
     int batch_mode;       /* batch: 0 auto, 1 one persistent kernel over a tile queue,
                              2 one CUDA graph of independent per-frame kernels */
-    int reserved[2];      /* must be zero */
+    int block_order;      /* class mapping, single frames and graph-of-kernels batches: 0 auto (bands for
+                             frames of 2^22 pixels or more, else raster), 1 patches in raster order,
+                             2 patches in bands of 32 patch rows, column by column within a band (the
+                             blocks resident at once cover a compact region; results are identical) */
+    int reserved;         /* must be zero */
 } ssilvb_tuning;
 
 /* One frame of a batch: its G-buffer, camera, parameters and outputs, with the same meaning
@@ -241,8 +245,8 @@ ssilvb_status ssilvb_gather_host_async(ssilvb_ctx *ctx, const ssilvb_gbuffer *gb
 ssilvb_status ssilvb_gather_batch(ssilvb_ctx *ctx, const ssilvb_frame *frames, int n_frames,
                                   struct CUstream_st *stream);
 
-/* Autotuner: times the launch choices (register budget, rows per work item, CUDA graph or not;
- * for n_frames == 1 also the single-frame mapping) on these frames, synchronising stream, and
+/* Autotuner: times the launch choices (register budget, rows per work item, CUDA graph or not,
+ * block order; for n_frames == 1 also the single-frame mapping) on these frames, synchronising stream, and
  * remembers the fastest for calls of the same kind (sector count, storage, thickness mode,
  * pixel-count class, largest N_d and N_s, single or batch).  The frames' outputs are written
  * (valid results).  *chosen (may be NULL) receives the winner. */

@@ -107,7 +107,7 @@ class Frame(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("mapping", ctypes.c_int), ("occupancy", ctypes.c_int), ("rows_per_tile", ctypes.c_int),
                 ("ctas_per_sm", ctypes.c_int), ("use_graph", ctypes.c_int), ("batch_mode", ctypes.c_int),
-                ("reserved", ctypes.c_int * 2)]
+                ("block_order", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
 _lib = None
@@ -367,8 +367,9 @@ class Context:
                                              ctypes.byref(t)))
         return t
 
-    def set_tuning(self, mapping=0, occupancy=0, rows_per_tile=0, ctas_per_sm=0, use_graph=0, batch_mode=0):
-        t = Tuning(mapping, occupancy, rows_per_tile, ctas_per_sm, use_graph, batch_mode)
+    def set_tuning(self, mapping=0, occupancy=0, rows_per_tile=0, ctas_per_sm=0, use_graph=0, batch_mode=0,
+                   block_order=0):
+        t = Tuning(mapping, occupancy, rows_per_tile, ctas_per_sm, use_graph, batch_mode, block_order)
         self._check(self.lib.ssilvb_set_tuning(self.handle, ctypes.byref(t)))
 
     def synchronize(self, stream=None):

@@ -130,8 +130,10 @@ ssilvb_status run_batch(ssilvb_ctx *ctx, const ssilvb_frame *frames, int n, cuda
         // One graph, one independent kernel node per frame (the single-frame kernel with its
         // parameters as a grid constant): the frames run concurrently, no tile queue.
         s.fparams.resize(n);
-        for (int i = 0; i < n; ++i)
+        for (int i = 0; i < n; ++i) {
             fill_params(s.fparams[i], &frames[i].gbuffer, &frames[i].camera, &frames[i].params, &frames[i].out);
+            apply_order(s.fparams[i], k);
+        }
         auto node_params = [&](int i, cudaKernelNodeParams &kp, void **args) {
             const void *fn = nullptr;
             dim3 grid, block;
@@ -314,7 +316,11 @@ ssilvb_status ssilvb_autotune(ssilvb_ctx *ctx, const ssilvb_frame *frames, int n
         k.mapping = SSILVB_MAP_CLASS;
         k.minb = minb;
         k.batch_mode = 2;
-        cands.push_back(k);
+        for (int order : {1, 2}) {  // the frames' blocks in raster order or in bands
+            k.order = order;
+            cands.push_back(k);
+        }
+        k.order = 0;  // the persistent kernel hands out its own work items
         for (int rows : {1, 2, 4})
             for (int graph : {1, 0}) {
                 k.batch_mode = 1;
@@ -355,16 +361,18 @@ ssilvb_status ssilvb_autotune(ssilvb_ctx *ctx, const ssilvb_frame *frames, int n
         KernelChoice best_s;
         float t_best_s = 1e30f;
         for (int mapping : {SSILVB_MAP_CLASS, SSILVB_MAP_TILE})
-            for (int minb : {8, 9}) {
-                if (mapping == SSILVB_MAP_TILE && minb == 8) continue;
-                KernelChoice k;
-                k.mapping = mapping;
-                k.minb = minb;
-                bool ok;
-                const float t = time_runs(ctx, frames, 1, st, k, true, &ok);
-                if (!ok) return SSILVB_ERR_CUDA;
-                if (t < t_best_s) { t_best_s = t; best_s = k; }
-            }
+            for (int minb : {8, 9})
+                for (int order : {1, 2}) {
+                    if (mapping == SSILVB_MAP_TILE && (minb == 8 || order == 2)) continue;
+                    KernelChoice k;
+                    k.mapping = mapping;
+                    k.minb = minb;
+                    k.order = mapping == SSILVB_MAP_CLASS ? order : 0;
+                    bool ok;
+                    const float t = time_runs(ctx, frames, 1, st, k, true, &ok);
+                    if (!ok) return SSILVB_ERR_CUDA;
+                    if (t < t_best_s) { t_best_s = t; best_s = k; }
+                }
         ctx->tuned[tune_key(&frames[0].gbuffer, &frames[0].params, 0)] = best_s;
         best = best_s;
         best.rows = best_b.rows;
@@ -379,6 +387,7 @@ ssilvb_status ssilvb_autotune(ssilvb_ctx *ctx, const ssilvb_frame *frames, int n
         chosen->ctas_per_sm = best.ctas_per_sm;
         chosen->use_graph = best.graph ? 1 : 2;
         chosen->batch_mode = best.batch_mode;
+        chosen->block_order = best.order;
     }
     return SSILVB_OK;
 }

@@ -37,7 +37,14 @@ struct KernelChoice {
     int ctas_per_sm = 0;             // batch: resident blocks per SM of the persistent grid (0 = occupancy)
     int graph = 1;                   // batch, persistent mode: launch through a CUDA graph
     int batch_mode = 2;              // batch: 1 persistent tile queue, 2 graph of per-frame kernels
+    int order = 0;                   // class mapping: 0 by frame size (fill_params), 1 raster, 2 bands
 };
+
+// Apply a launch choice's block order to a frame's parameters (order 0 keeps fill_params's choice).
+inline void apply_order(GatherParams &P, const KernelChoice &k) {
+    if (k.order == 1) P.band_rows = 1;
+    else if (k.order == 2) P.band_rows = 32;
+}
 
 // Default register budget of the class and batch kernels (measured at 4K, CUDA events): 8 blocks of
 // 128 threads per SM for N_b = 32 (1 % faster than 9), 9 for N_b = 64 and 128 (1.5 % faster than 8).
@@ -112,7 +119,7 @@ struct ssilvb_ctx {
     cudaEvent_t host_entry = nullptr;
     ssilvb::HostLane sync_lane, async_lane[2];
     int async_next = 0;
-    ssilvb_tuning tuning = {SSILVB_MAP_AUTO, 0, 0, 0, 0, 0, {0, 0}};
+    ssilvb_tuning tuning = {SSILVB_MAP_AUTO, 0, 0, 0, 0, 0, 0, 0};
     cudaStream_t cap_stream = nullptr;     // private stream the batch graphs are captured on
     std::vector<ssilvb::BatchSlot> slots;  // ring of in-flight batches
     int next_slot = 0;

@@ -278,7 +278,9 @@ void fill_params(ssilvb::GatherParams &P, const ssilvb_gbuffer *g, const ssilvb_
     if (na > 0) ambient_form(c->view_to_world, p->sh_rgb, P.amb_b, P.amb_q);
 }
 
-cudaError_t launch_single(const GatherParams &P, int nb, int fmt, bool inf_t, const KernelChoice &k, cudaStream_t s) {
+cudaError_t launch_single(const GatherParams &P0, int nb, int fmt, bool inf_t, const KernelChoice &k, cudaStream_t s) {
+    GatherParams P = P0;  // passed to the kernel by value
+    apply_order(P, k);
     if (nb == 32) return launch_single_nb32(P, fmt, inf_t, k, s);
     if (nb == 64) return launch_single_nb64(P, fmt, inf_t, k, s);
     return launch_single_nb128(P, fmt, inf_t, k, s);
@@ -329,6 +331,7 @@ KernelChoice resolve_choice(const ssilvb_ctx *ctx, const TuneKey &key) {
     if (t.ctas_per_sm) k.ctas_per_sm = t.ctas_per_sm;
     if (t.use_graph) k.graph = t.use_graph == 1;
     if (t.batch_mode) k.batch_mode = t.batch_mode;
+    if (t.block_order) k.order = t.block_order;
     return k;
 }
 
@@ -427,8 +430,9 @@ ssilvb_status ssilvb_set_tuning(ssilvb_ctx *ctx, const ssilvb_tuning *tuning) {
         return fail(ctx, SSILVB_ERR_INVALID_ARG, "use_graph must be 0, 1 or 2");
     if (tuning->batch_mode < 0 || tuning->batch_mode > 2)
         return fail(ctx, SSILVB_ERR_INVALID_ARG, "batch_mode must be 0, 1 or 2");
-    for (int i = 0; i < 2; ++i)
-        if (tuning->reserved[i]) return fail(ctx, SSILVB_ERR_INVALID_ARG, "reserved tuning fields must be zero");
+    if (tuning->block_order < 0 || tuning->block_order > 2)
+        return fail(ctx, SSILVB_ERR_INVALID_ARG, "block_order must be 0, 1 or 2");
+    if (tuning->reserved) return fail(ctx, SSILVB_ERR_INVALID_ARG, "reserved tuning field must be zero");
     ctx->tuning = *tuning;
     return SSILVB_OK;
 }

@@ -76,11 +76,12 @@ UNEVEN = [
 ]
 
 
-@pytest.mark.parametrize("mode,rows,graph", [(1, 1, 1), (1, 2, 2), (1, 4, 1), (1, 3, 2), (2, 0, 0)])
-def test_batch_equals_single(ctx, mode, rows, graph):
+@pytest.mark.parametrize("mode,rows,graph,order", [(1, 1, 1, 0), (1, 2, 2, 0), (1, 4, 1, 0), (1, 3, 2, 0), (2, 0, 0, 0),
+                                                  (2, 0, 0, 2)])
+def test_batch_equals_single(ctx, mode, rows, graph, order):
     import torch
     frames, keep, outs, gbs, prms = _frames(ctx, UNEVEN)
-    ctx.set_tuning(rows_per_tile=rows, use_graph=graph, batch_mode=mode)
+    ctx.set_tuning(rows_per_tile=rows, use_graph=graph, batch_mode=mode, block_order=order)
     ctx.gather_batch(frames)
     torch.cuda.synchronize()
     ctx.set_tuning()

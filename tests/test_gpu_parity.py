@@ -90,6 +90,31 @@ def test_fp16_storage(ctx, f16):
     check_parity(g, prm, noise, sh, res)
 
 
+@pytest.mark.parametrize("W,H,nb", [(150, 77, 32), (333, 1100, 32), (333, 1100, 64), (97, 1601, 128)])
+def test_block_orders_bit_identical(ctx, W, H, nb):
+    """The class-mapped blocks in raster order of patches or in bands of 32 patch rows (the order
+    the library picks for frames of 2^22 pixels or more, forced here on small frames): the same
+    patches, so identical bits.  1100 and 1601 rows give 69 and 101 patch rows, so full bands and a
+    shorter last one; a ragged right edge (333, 97 pixels) leaves part of the last patch column
+    empty.  An unknown order is rejected."""
+    g = scenegen.render(31, W, H, 10, 4)
+    prm = Params(num_slices=2, steps_per_side=7, sector_count=nb, ambient_cones=2)
+    noise, sh = scenegen.ign_table(), scenegen.sh_environment(7)
+    results = []
+    try:
+        for order in (1, 2, 0):
+            ctx.set_tuning(block_order=order)
+            results.append(run_gpu(ctx, g, prm, noise, sh))
+        with pytest.raises(Exception, match="block_order"):
+            ctx.set_tuning(block_order=3)
+    finally:
+        ctx.set_tuning()
+    for r in results[1:]:
+        for a, b in zip(results[0], r):
+            assert np.array_equal(a, b)
+    check_parity(g, prm, noise, sh, results[0], pixels=sample_pixels(H, W, 20000, 5))
+
+
 @pytest.mark.parametrize("nb,step_mode,f16", [(32, 0, True), (64, 1, False), (128, 0, False)])
 def test_launch_choices_bit_identical(ctx, nb, step_mode, f16):
     """Every single-frame launch choice (class-strided warps with the 8- or 9-block register
