@@ -1,4 +1,4 @@
-// Launch wrappers for one sector count (included by launch_nb32.cu and launch_nb64.cu).
+// Launch wrappers for one sector count (included by launch_nb32.cu, launch_nb64.cu and launch_nb128.cu).
 #pragma once
 
 #include "internal.h"
