@@ -83,6 +83,8 @@ def _load():
                                                 ctypes.c_void_p]
         lib.orc32_acos_sweep.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
         lib.orc32_rsqrt_sweep.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int]
+        lib.orc32_ambient_form.argtypes = [vp, vp, vp, vp]
+        lib.orc32_ambient_form.restype = None
         lib.orc32_rsqrt_sweep.restype = ctypes.c_double
         _lib = lib
     return _lib
@@ -259,6 +261,17 @@ def acos32_sweep(stride: int = 16):
 
 def rsqrt32_sweep(lo: float, hi: float, n: int) -> float:
     return _load().orc32_rsqrt_sweep(lo, hi, n)
+
+
+def ambient_form32(R, sh):
+    """The replica's per-launch ambient coefficients (b[3][3], Q[3][6] as xx, yy, zz, xy, xz, yz) for
+    the view-to-world rotation R (3x3) and the SH coefficients sh (27, [m][rgb])."""
+    Rf = np.ascontiguousarray(np.asarray(R, dtype=np.float32).reshape(9))
+    shf = np.ascontiguousarray(np.asarray(sh, dtype=np.float32).reshape(27))
+    b = np.zeros(9, np.float32)
+    q = np.zeros(18, np.float32)
+    _load().orc32_ambient_form(Rf.ctypes.data, shf.ctypes.data, b.ctypes.data, q.ctypes.data)
+    return b.reshape(3, 3), q.reshape(3, 6)
 
 
 def lib():

@@ -101,5 +101,9 @@ uint64_t orc64_sector_mask(double A, double B, int nb, int hit_rule);
 void orc64_sector_mask_words(double A, double B, int nb, int hit_rule, uint64_t *out2);
 /* The replica's O(1) mask as two 64-bit words, for tests. */
 void orc32_sector_mask_words(float A, float B, int nb, int hit_rule, uint64_t *out2);
+/* The replica's per-launch ambient coefficients: the SH environment sh[27] seen through the
+ * view-to-world rotation R[9] as L(a) = b.a + a^T Q a per channel; b_out[9], q_out[18]
+ * (Q as xx, yy, zz, xy, xz, yz). */
+void orc32_ambient_form(const float *R, const float *sh, float *b_out, float *q_out);
 
 #endif

@@ -248,6 +248,17 @@ static void setup32(const orc_problem *pb, ctx32 *c) {
     if (c->na > 0) ambient_form32(pb->view_to_world, pb->sh, c->amb_b, c->amb_q);
 }
 
+/* The per-launch ambient coefficients above, for a pin test: b_out[3 channel + j] = b_j,
+ * q_out[6 channel + m] = Q's entry m (xx, yy, zz, xy, xz, yz). */
+void orc32_ambient_form(const float *R, const float *sh, float *b_out, float *q_out) {
+    float b[3][3], q[3][6];
+    ambient_form32(R, sh, b, q);
+    for (int ch = 0; ch < 3; ++ch) {
+        for (int j = 0; j < 3; ++j) b_out[3 * ch + j] = b[ch][j];
+        for (int m = 0; m < 6; ++m) q_out[6 * ch + m] = q[ch][m];
+    }
+}
+
 /* One pixel of the replica.  cnt[7] accumulates the counters of orc32_pixels.  runs (may be NULL):
  * this pixel's [N_d][2][N_s] block of (lo, hi) sector runs, written for every step (0, 0 where the
  * step sets no sector).  ep (may be NULL): this pixel's [N_d][2][N_s] block of (X_f, X_b) pairs,

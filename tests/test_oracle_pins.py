@@ -562,6 +562,37 @@ def test_ambient_cones_follow_the_projected_normal():
 
 # --- the binary32 replica against the FP64 oracle on a seeded frame ---------------------------
 
+def test_replica_ambient_form_is_the_sh_sum():
+    """The binary32 replica weights its ambient cones against the SH environment written once per
+    launch as a quadratic form of the view-space direction, b.a + a^T Q a (Section 3.2's ambient
+    light; the FP64 oracle evaluates the nine basis functions instead).  For random rotations,
+    random coefficients and random unit directions the form must equal the 3-band real SH sum of
+    the world direction R a, evaluated here from the basis definitions (Y00 = 1/(2 sqrt(pi)),
+    Y1m = sqrt(3/(4 pi)) (y, z, x), Y2m = sqrt(15/pi)/2 (xy, yz, xz), sqrt(5/pi)/4 (3z^2 - 1),
+    sqrt(15/pi)/4 (x^2 - y^2)), to the binary32 rounding of the coefficients.  A dropped constant
+    term, a wrong band-2 factor or an unrotated direction fails it."""
+    rng = np.random.default_rng(41)
+    c0, c1 = 0.5 * math.sqrt(1.0 / math.pi), math.sqrt(3.0 / (4.0 * math.pi))
+    c2, c3, c4 = 0.5 * math.sqrt(15.0 / math.pi), 0.25 * math.sqrt(5.0 / math.pi), 0.25 * math.sqrt(15.0 / math.pi)
+    for trial in range(8):
+        R, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+        sh = rng.uniform(-1.0, 1.0, size=(9, 3))
+        R32, sh32 = R.astype(np.float32), sh.astype(np.float32)
+        b, q = oracle.ambient_form32(R32, sh32)
+        a = rng.normal(size=(200, 3))
+        a /= np.linalg.norm(a, axis=1, keepdims=True)
+        w = a @ R32.astype(np.float64).T
+        x, y, z = w[:, 0], w[:, 1], w[:, 2]
+        Y = np.stack([np.full_like(x, c0), c1 * y, c1 * z, c1 * x, c2 * x * y, c2 * y * z,
+                      c3 * (3.0 * z * z - 1.0), c2 * x * z, c4 * (x * x - y * y)], axis=1)
+        direct = Y @ sh32.astype(np.float64)  # [200, 3]
+        for ch in range(3):
+            Q = q[ch].astype(np.float64)
+            form = (a @ b[ch].astype(np.float64) + Q[0] * a[:, 0] ** 2 + Q[1] * a[:, 1] ** 2 + Q[2] * a[:, 2] ** 2
+                    + 2.0 * (Q[3] * a[:, 0] * a[:, 1] + Q[4] * a[:, 0] * a[:, 2] + Q[5] * a[:, 1] * a[:, 2]))
+            assert np.abs(form - direct[:, ch]).max() < 2e-6, (trial, ch)
+
+
 def test_replica_vs_fp64_on_256():
     w = scenegen.workload_256()
     prob = oracle.Problem(w.gbuf, w.params, w.noise)
