@@ -20,7 +20,10 @@
  *     0x5f3759df - (bits >> 1) (Lomont, "Fast inverse square root", 2003)
  *     refined by three Newton steps y <- y (1.5 - 0.5 x y^2);
  *   - the back endpoint uses l_b.v = l.v - t and |l_b|^2 = |l|^2 - 2t (l.v) + t^2,
- *     which follow from l_b = l - t v (v = -p/|p|).
+ *     which follow from l_b = l - t v (v = -p/|p|);
+ *   - the ambient cones weigh the SH environment written once per call as a quadratic form
+ *     of the view-space direction, b.a + a^T Q a (coefficients in FP64, rounded once), so a
+ *     slice's cones reduce to five weighted sums of their direction cosines and sines.
  * Op counts (the algorithmic work used by the roofline) are accumulated per
  * block, one per IEEE add/sub/mul/fma/div/sqrt, compare, select, min/max,
  * conversion, shift, logic op and popcount.
