@@ -166,7 +166,7 @@ typedef struct {
                              2 one CUDA graph of independent per-frame kernels */
     int block_order;      /* class mapping, single frames and graph-of-kernels batches: 0 auto (bands for
                              frames of 2^22 pixels or more, else raster), 1 patches in raster order,
-                             2 patches in bands of 32 patch rows, column by column within a band (the
+                             2 patches in bands of about 32 patch rows, column by column within a band (the
                              blocks resident at once cover a compact region; results are identical) */
     int reserved;         /* must be zero */
 } ssilvb_tuning;

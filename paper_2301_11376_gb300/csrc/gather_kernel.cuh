@@ -54,7 +54,8 @@ struct GatherParams {
     size_t out1_pitch;     // elements (floats)
     int W, H;
     int y0, y1;            // centre-pixel rows [y0, y1) this launch covers (samples read the whole frame)
-    int band_rows;         // class mapping: blocks in bands of this many patch rows (1: raster order of patches)
+    int band_rows;         // class mapping: patches run in bands of about this many patch rows, column by
+                           // column within a band (1: raster order); the launch grid carries it
     int nd, ns, na;
     int hit_rule, step_mode, gi;
     // per-launch binary32 constants
@@ -718,9 +719,9 @@ __global__ void __launch_bounds__(256) gather_tile_kernel(const __grid_constant_
 // one 4x4 noise class, so its 32 lanes share the slice directions and step offsets: their samples
 // land on neighbouring pixels and their skip decisions mostly agree (a compact patch agrees more
 // often than a 128-pixel row).  The 4 warps of a block take the 4 column classes of one row
-// class; blockIdx.x = 4 * patch column + row class keeps a patch's blocks adjacent, blockIdx.y is
-// the patch row within rows [y0, y1) (or, with band_rows, the patches are renumbered band by band).
-// MINB: blocks of 128 threads per SM the register budget is sized for.
+// class; the row class is the fastest block index, so a patch's blocks run next to each other
+// (the launch grid orders the patches: see the kernel).  MINB: blocks of 128 threads per SM the
+// register budget is sized for.
 __device__ __forceinline__ void patch_pixel(int patch_x, int patch_y, int row_class, int &x, int &y) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     x = patch_x * 32 + 4 * (lane & 7) + w;
@@ -729,23 +730,12 @@ __device__ __forceinline__ void patch_pixel(int patch_x, int patch_y, int row_cl
 
 template <int NB, int FMT, bool INF_T, int STEP_MODE, int MINB>
 __global__ void __launch_bounds__(128, MINB) gather_class_kernel(const __grid_constant__ GatherParams P) {
-    int pcol = blockIdx.x >> 2, prow = blockIdx.y;
-    // Patches in launch order taken band by band (band_rows patch rows each), column by column
-    // within a band: the blocks resident at once then cover a compact region of a large frame
-    // instead of a strip across it, and their indirect-light fetches share more of the L2.  A
-    // bijection of the same patches (the last band may be shorter), so results are unchanged; one
-    // patch row per band is the raster order.  For N_b = 32 the renumbering is skipped where it
-    // changes nothing, for 64 and 128 it always runs: of the two forms, measured on 3840 x 2160 and
-    // smaller frames, each is the faster for those sector counts (the code around it compiles
-    // differently).
-    if (NB != 32 || P.band_rows > 1) {
-        const int PX = gridDim.x >> 2, PY = gridDim.y, TH = max(P.band_rows, 1);
-        const int p = blockIdx.y * PX + pcol;  // the patch's index in raster order
-        const int band = p / (PX * TH), r = p - band * (PX * TH);
-        const int th = min(TH, PY - band * TH);
-        pcol = r / th;
-        prow = band * TH + (r - pcol * th);
-    }
+    // The grid is (4 x band height, patch columns, bands) and blocks are numbered x fastest, so the
+    // patches run band by band, column by column within a band (a band of one patch row is the
+    // raster order).  On a large frame the blocks resident at once then cover a compact region
+    // rather than a strip across the frame, and their indirect-light fetches share the L2.  Rows
+    // past the launch's last one (a short last band) exit below.
+    const int pcol = blockIdx.y, prow = blockIdx.z * (int)(gridDim.x >> 2) + (int)(blockIdx.x >> 2);
     int x, y;
     patch_pixel(pcol, prow, blockIdx.x & 3, x, y);
     y += P.y0;

@@ -5,6 +5,19 @@
 
 namespace ssilvb {
 
+// Launch grid of the class mapping: (4 row classes x TH patch rows, patch columns, bands of TH patch
+// rows), TH = 1 for the raster order, else the band height closest to P.band_rows that splits the
+// launch's patch rows into equal bands (the last one at most a row short).
+inline dim3 class_grid(const GatherParams &P) {
+    const int px = (P.W + 31) / 32, py = (P.y1 - P.y0 + 15) / 16;
+    int th = 1;
+    if (P.band_rows > 1) {
+        const int nbands = (py + P.band_rows - 1) / P.band_rows;
+        th = (py + nbands - 1) / nbands;
+    }
+    return dim3(4 * th, px, (py + th - 1) / th);
+}
+
 template <int NB, int FMT, bool INF_T, int SM>
 cudaError_t launch_single_t(const GatherParams &P, const KernelChoice &k, cudaStream_t s) {
     if (k.mapping == SSILVB_MAP_TILE) {
@@ -12,7 +25,7 @@ cudaError_t launch_single_t(const GatherParams &P, const KernelChoice &k, cudaSt
         gather_tile_kernel<NB, FMT, INF_T, SM><<<grid, 256, 0, s>>>(P);
     } else {
         // 32 x 16 pixel patches, 4 row classes each (see gather_class_kernel)
-        dim3 grid(4 * ((P.W + 31) / 32), (P.y1 - P.y0 + 15) / 16);
+        const dim3 grid = class_grid(P);
         if (k.minb == 8) gather_class_kernel<NB, FMT, INF_T, SM, 8><<<grid, 128, 0, s>>>(P);
         else gather_class_kernel<NB, FMT, INF_T, SM, 9><<<grid, 128, 0, s>>>(P);
     }
@@ -46,7 +59,7 @@ void single_node_t(const GatherParams &P, const KernelChoice &k, const void **fn
     } else {
         *fn = k.minb == 8 ? reinterpret_cast<const void *>(gather_class_kernel<NB, FMT, INF_T, SM, 8>)
                           : reinterpret_cast<const void *>(gather_class_kernel<NB, FMT, INF_T, SM, 9>);
-        *grid = dim3(4 * ((P.W + 31) / 32), (P.y1 - P.y0 + 15) / 16);
+        *grid = class_grid(P);
         *block = dim3(128);
     }
 }

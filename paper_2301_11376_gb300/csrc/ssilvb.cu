@@ -228,9 +228,9 @@ void fill_params(ssilvb::GatherParams &P, const ssilvb_gbuffer *g, const ssilvb_
     P.H = g->height;
     P.y0 = 0;
     P.y1 = g->height;
-    // Frames of 2^22 pixels or more (4K) run their class-mapped blocks in bands of 32 patch rows:
-    // measured at 4K 4 % faster (N_b 64: 5 %); at 1080p and 1440p the raster order (bands of one
-    // patch row) is 2-4 % faster, so smaller frames keep it.
+    // Frames of 2^22 pixels or more (4K) run their class-mapped patches in bands of about 32 patch
+    // rows (27 at 2160 rows): measured at 4K 4 % faster (N_b 64: 4 %); at 1080p and 1440p the raster
+    // order (bands of one patch row) is 2-4 % faster, so smaller frames keep it.
     P.band_rows = (long long)g->width * g->height >= (1LL << 22) ? 32 : 1;
     P.nd = p->num_slices;
     P.ns = p->steps_per_side;

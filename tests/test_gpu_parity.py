@@ -92,11 +92,12 @@ def test_fp16_storage(ctx, f16):
 
 @pytest.mark.parametrize("W,H,nb", [(150, 77, 32), (333, 1100, 32), (333, 1100, 64), (97, 1601, 128)])
 def test_block_orders_bit_identical(ctx, W, H, nb):
-    """The class-mapped blocks in raster order of patches or in bands of 32 patch rows (the order
-    the library picks for frames of 2^22 pixels or more, forced here on small frames): the same
-    patches, so identical bits.  1100 and 1601 rows give 69 and 101 patch rows, so full bands and a
-    shorter last one; a ragged right edge (333, 97 pixels) leaves part of the last patch column
-    empty.  An unknown order is rejected."""
+    """The class-mapped blocks in raster order of patches or in bands of about 32 patch rows (the
+    order the library picks for frames of 2^22 pixels or more, forced here on small frames): the
+    same patches, so identical bits.  1100 and 1601 rows give 69 and 101 patch rows: three bands of
+    23, and four of 26 with the last one three rows short (its blocks past the frame exit); a ragged
+    right edge (333, 97 pixels) leaves part of the last patch column empty.  An unknown order is
+    rejected."""
     g = scenegen.render(31, W, H, 10, 4)
     prm = Params(num_slices=2, steps_per_side=7, sector_count=nb, ambient_cones=2)
     noise, sh = scenegen.ign_table(), scenegen.sh_environment(7)
