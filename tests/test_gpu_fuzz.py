@@ -2,8 +2,8 @@
 parameter of the ABI in random combination (N_d 1-16, N_s 1-64, N_b 32/64/128, both hit rules,
 both step modes, finite and infinite thickness, thickness slope, 0-8 ambient cones, GI on/off),
 FP32 or FP16 storage, no noise / the built-in table / a random table, and camera intrinsics and
-view rotation perturbed away from the scene generator's symmetric camera.  Every gate of
-check_parity on every pixel, through the C ABI."""
+view rotation perturbed away from the scene generator's symmetric camera, the patches in raster
+or band order.  Every gate of check_parity on every pixel, through the C ABI."""
 import math
 
 import pytest
@@ -29,7 +29,13 @@ def ctx():
 @pytest.mark.parametrize("k", range(40))
 def test_random_problem(ctx, k):
     g, prm, noise, table, sh = case(k)
-    res = run_gpu(ctx, g, prm, noise, sh)
+    # odd cases run the class-mapped patches in bands (the order of large frames), even ones in
+    # raster order: both orders over the random sizes
+    ctx.set_tuning(block_order=1 + k % 2)
+    try:
+        res = run_gpu(ctx, g, prm, noise, sh)
+    finally:
+        ctx.set_tuning()
     # The agreement and clear-pixel floors only guard against a vacuous comparison; random slice
     # counts up to 16 make fully clear pixels rarer.  The floor/ceil rule with infinite thickness puts
     # every sample in the tangent plane of a flat surface on a rounding boundary (its run ends on the
