@@ -841,10 +841,8 @@ def main():
                 "roofline_frac": (ops_nb / (m / 1e3) / (SM_COUNT_GB300 * FP32_LANES_PER_SM * 2.070e9)
                                   if ops_nb is not None else None),
                 "ops_per_frame": ops_nb,
-                "accuracy": ("masks bit-exact against the binary32 replica on the whole frame "
-                             "(tests/test_gpu_parity.py)" if nb == 64 else
-                             "masks bit-exact against the binary32 replica on 12k sampled pixels "
-                             "(tests/test_gpu_parity.py)")}
+                "accuracy": "masks bit-exact against the binary32 replica on the whole frame "
+                            "(tests/test_gpu_parity.py)"}
         if g.normal.dtype == np.float16:
             # the same workload with the other FP16 layout, for comparison (same results bit for bit)
             other = (torch.from_numpy(np.ascontiguousarray(g.normal)).to(dev),

@@ -199,7 +199,7 @@ def test_4k_precision_form_sampled(ctx, nb):
     assert info["agree"] > 0.98
 
 
-@pytest.mark.parametrize("nb", [32, 64])
+@pytest.mark.parametrize("nb", [32, 64, 128])
 def test_4k_full_frame_every_pixel(ctx, nb):
     """The benchmark workload in full, every gate on every pixel: all 8.29 M x 4 slice masks
     bit-exact against the binary32 replica, every pixel's AO, GI and ambient within 1e-4 of the
