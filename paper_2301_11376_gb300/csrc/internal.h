@@ -47,9 +47,10 @@ inline void apply_order(GatherParams &P, const KernelChoice &k) {
 }
 
 // Default register budget of the class and batch kernels (CUDA events): 8 blocks of 128 threads per
-// SM for N_b = 32 (at 4K 3.99 against 4.21 ms with 9), 9 for N_b = 64 (4.32 against 4.35 ms) and 128
-// (at 4K 4.77 against 4.72 ms with 8, but at 1080p 5-10 % faster than 8).
-inline int default_minb(int nb) { return nb == 32 ? 8 : 9; }
+// SM for N_b = 32 (at 4K 3.99 against 4.21 ms with 9); for N_b = 64 and 128, 8 on single frames of
+// 2^22 pixels or more (at 4K 4.31 against 4.36 ms and 4.72 against 4.77 ms) and 9 otherwise (the
+// 1080p trend rows at N_b 128 are 5-10 % faster with 9).
+inline int default_minb(int nb, bool large_frame = false) { return nb == 32 || large_frame ? 8 : 9; }
 
 cudaError_t launch_single_nb32(const GatherParams &P, int fmt, bool inf_t, const KernelChoice &k, cudaStream_t s);
 cudaError_t launch_single_nb64(const GatherParams &P, int fmt, bool inf_t, const KernelChoice &k, cudaStream_t s);

@@ -321,7 +321,8 @@ TuneKey tune_key(const ssilvb_gbuffer *g, const ssilvb_params *p, int batch) {
 
 KernelChoice resolve_choice(const ssilvb_ctx *ctx, const TuneKey &key) {
     KernelChoice k;
-    k.minb = default_minb(key.nb);
+    // size_class = ceil(log2(pixels)): 23 and up is more than 2^22 pixels (3840 x 2160 is 2^22.98)
+    k.minb = default_minb(key.nb, key.batch == 0 && key.size_class >= 23);
     auto it = ctx->tuned.find(key);
     if (it != ctx->tuned.end()) k = it->second;
     const ssilvb_tuning &t = ctx->tuning;
